@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of Fourier-accelerated steepest-descent Landau gauge fixing.
+
+Workload (one step = one complete gauge fixing): an SU(3) 32^4 lattice in FP64
+with 12-real link storage, alpha = 0.08, run until theta < 1e-15, on synthetic
+rough-gauge configurations of roughness eps in {0.15, 0.3, 0.5} (stand-ins for
+the paper's three Wilson-action couplings), cycled over the steps.  The metric
+is iterations per second over the timed steps (all ranks together) and the
+time-to-theta of each configuration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm times the FP64 CPU oracle on the host cores on the same
+workload (one oracle iteration per step).  Under torchrun each rank fixes its
+own configurations (independent replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SD iters/s & time-to-theta<1e-15, 32^4 SU(3), FP64 vs mixed; % of HBM peak"
+FP64_PEAK_GFLOPS = 1250.0  # GB300 dense FP64 (nominal, 152 SMs); the probe measured 1190
+EPS = (0.15, 0.3, 0.5)
+SEEDS = (3201, 3202, 3203)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dims", default="32,32,32,32")
+    ap.add_argument("--alpha", type=float, default=0.08)
+    ap.add_argument("--tol", type=float, default=1e-15)
+    ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(dims):
+    return "SU(3) %s FP64 Fourier-accelerated steepest descent, 12-real links, alpha=0.08, theta<1e-15, eps %s" % (
+        "x".join(str(d) for d in dims), "/".join(str(e) for e in EPS))
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def configs(dims, rank):
+    from paper_1301_3460_gb300 import inputs
+
+    return [inputs.rough_gauge_field(dims, e, s + 1000 * rank) for e, s in zip(EPS, SEEDS)]
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(n)
+        if not sm:
+            return None
+        load = [v for v in sm if mx and v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- traffic record
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1301_3460_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel, dims, precision):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if rec.get("csrc_hash") != csrc_hash():
+        return None
+    key = "%s/%s/fp%d" % (kernel, "x".join(map(str, dims)), precision)
+    v = rec.get("per_launch_bytes", {}).get(key)
+    return float(v) if v is not None else None
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args, dims):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+
+    U = configs(dims, 0)
+    t_all = []
+    n_it = 0
+    for k in range(args.warmup + args.steps):
+        Ui = U[k % len(U)]
+        t0 = time.perf_counter()
+        r = orc.fix(dims, Ui, alpha=args.alpha, tol=0.0, max_iter=1)
+        dt = time.perf_counter() - t0
+        U[k % len(U)] = r["U"]
+        if k >= args.warmup:
+            t_all.append(dt)
+            n_it += r["iters"]
+    T = sum(t_all)
+    value = n_it / T
+    cores = orc.threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                         "sample": "one oracle iteration per step on the %s configurations (eps %s)" % (
+                             "x".join(map(str, dims)), "/".join(map(str, EPS)))},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, dims):
+    import torch
+
+    from paper_1301_3460_gb300 import lgf, roofline
+
+    ws, rank, local = dist()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = tdist
+    lgf.load()
+    host = configs(dims, rank)
+    V = host[0].shape[1]
+    stream = torch.cuda.current_stream()
+    dev = [torch.from_numpy(U).to("cuda") for U in host]
+    lat = lgf.Lattice(dims, stream=stream)
+
+    def step(i):
+        lat.set_links(dev[i % len(dev)])
+        return lat.fix(args.alpha, args.tol, args.max_iter)
+
+    for k in range(args.warmup):
+        step(k)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    info = []
+    ev[0].record(stream)
+    for k in range(args.steps):
+        info.append(step(k))
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+    per_step = [ev[k].elapsed_time(ev[k + 1]) / 1000.0 for k in range(args.steps)]
+    T = sum(per_step)
+    iters = sum(r["iters"] for r in info)
+    if pg:
+        t = torch.tensor([T], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        n = torch.tensor([iters], device="cuda", dtype=torch.float64)
+        pg.all_reduce(n, op=pg.ReduceOp.SUM)
+        T, iters = float(t.item()), int(n.item())
+    value = iters / T
+    launches = sum(3 + 5 * max(r["iters"], 1) for r in info)
+    ttt = {}
+    for k, r in enumerate(info):
+        ttt.setdefault(str(EPS[k % len(EPS)]), dict(iters=r["iters"], ms=1000 * per_step[k], F=r["F"],
+                                                     theta=r["theta"], converged=r["converged"]))
+
+    # end to end through the C ABI from pinned host memory, copies included
+    e2e = None
+    if not args.no_e2e:
+        pin_in = [torch.from_numpy(U).pin_memory() for U in host]
+        pin_out = torch.empty((4, V, 3, 3), dtype=torch.complex128).pin_memory()
+        nbytes = pin_in[0].numel() * 16
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = 0
+        for k in range(args.steps):
+            lat.set_links(pin_in[k % len(pin_in)])
+            n_e2e += lat.fix(args.alpha, args.tol, args.max_iter)["iters"]
+            lat._lib.lgf_get_links(lat._h, lgf.ctypes.c_void_p(pin_out.data_ptr()), 0)
+        torch.cuda.synchronize()
+        Te = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([Te], device="cuda", dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            n = torch.tensor([n_e2e], device="cuda", dtype=torch.float64)
+            pg.all_reduce(n, op=pg.ReduceOp.SUM)
+            Te, n_e2e = float(t.item()), int(n.item())
+        e2e = {"value": n_e2e / Te, "unit": "iters/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # per-kernel durations (CUDA events around each launch) on the eps = 0.3 configuration
+    lat.set_links(dev[1])
+    ms = lat.time_kernels(args.alpha, n_iter=8, precision=64)
+    per = roofline.per_site(dims, 64)
+    kern = max(ms, key=lambda k: ms[k])
+    sec = ms[kern] / 1000.0
+    flops = per[kern]["flops"] * V
+    byts = per[kern]["bytes"] * V
+    traffic = traffic_record(kern, dims, 64)
+    roof = {"bound": "alu", "kernel": kern, "achieved": flops / sec / 1e9, "peak": FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s", "frac": flops / sec / 1e9 / FP64_PEAK_GFLOPS, "traffic": traffic,
+            "peak_source": "GB300 nominal dense FP64 (recipe table); measured FMA probe 1190 GFLOP/s",
+            "hbm_achieved_gbs": byts / sec / 1e9}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        roof["hbm_frac_of_measured"] = roof["hbm_achieved_gbs"] / float(peaks["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    kernels = {k: {"ms": ms[k], "gflops": per[k]["flops"] * V / ms[k] / 1e6, "gbs": per[k]["bytes"] * V / ms[k] / 1e6}
+               for k in ms}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+
+        t0 = time.perf_counter()
+        r = orc.fix(dims, host[1], alpha=args.alpha, tol=0.0, max_iter=args.cpu_iters)
+        dt = time.perf_counter() - t0
+        cpu = {"value": r["iters"] / dt, "unit": "iters/s", "cores": orc.threads(), "kind": "oracle",
+               "sample": "first %d iterations of the eps=0.3 %s configuration" % (r["iters"], "x".join(map(str, dims)))}
+
+    lat.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol,
+                       "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
+                       % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
+            "time_to_theta": ttt, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    dims = tuple(int(v) for v in args.dims.split(","))
+    if args.impl == "reference":
+        return run_reference(args, dims)
+    return run_ours(args, dims)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,156 @@
+/*
+ * lgf.h -- C ABI of the GB300 (sm_103a) library for Landau gauge fixing of 4D
+ * SU(3) lattice gauge fields by Fourier-accelerated steepest descent.
+ *
+ * Method (Cardoso, Silva, Oliveira, Bicudo, arXiv:1301.3460): Landau gauge is
+ * the maximum over gauge transformations g of the functional (introduction)
+ *     F_U[g] = 1/(N_d N_c V) sum_x sum_mu Re Tr[g(x) U_mu(x) g^dag(x+mu)],
+ * reached by steepest descent with Fourier acceleration (introduction); the
+ * paper's runs use alpha = 0.08 and stop at theta < 1e-15 (description of the
+ * 32^4 comparison) and keep links as 12 reals (description of the GPU set-up).
+ * One iteration on the current links U:
+ *     M(x)     = sum_mu [U_mu(x-mu) - U_mu(x)]
+ *     Delta(x) = (M - M^dag) - Tr(M - M^dag)/3
+ *     theta    = 1/(N_c V) sum_x Tr[Delta Delta^dag],   F = F_U[1]
+ *     stop if theta < tol (the test is made before an update)
+ *     Delta~   = IFFT[ p2max/p2(k) FFT[Delta](k) ] / V,  k = 0 removed,
+ *                p2(k) = sum_mu 4 sin^2(pi k_mu/L_mu)
+ *     g(x)     = reunit(1 + alpha/2 Delta~(x))   (row Gram-Schmidt onto SU(3))
+ *     U_mu(x) <- g(x) U_mu(x) g^dag(x+mu),  G(x) <- g(x) G(x)
+ *
+ * Conventions
+ *   - Every function returns an lgf_status; none throws or aborts.
+ *   - Lattice extents dims[4] = {Lx, Ly, Lz, Lt}; site s = x + Lx*(y + Ly*(z + Lz*t)).
+ *   - Link arrays are complex128 [4][V][3][3] (mu, site, row, column), real and
+ *     imaginary parts interleaved, row-major: 18 doubles per link.  Gauge
+ *     transformations are [V][3][3] complex128.
+ *   - Pointers are owned by the caller; the library copies in and out.  A flag
+ *     on_device = 1 means the pointer is device memory of the current CUDA
+ *     device, 0 means host memory (pinned or pageable).
+ *   - The context owns all of its device memory and runs its work on the stream
+ *     given by lgf_set_stream (default: the legacy default stream).  Calls on
+ *     one context must not overlap; separate contexts are independent.
+ *   - No CPU fallback exists: without a usable CUDA device lgf_create fails
+ *     with LGF_ERR_CUDA.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgf_ctx lgf_ctx;
+
+typedef enum {
+    LGF_OK = 0,
+    LGF_ERR_ARG = 1,              /* null pointer, bad parameter value */
+    LGF_ERR_CUDA = 2,             /* a CUDA call failed (no device, out of memory, launch error) */
+    LGF_ERR_NOT_SU3 = 3,          /* input links are not in SU(3) to 1e-12 */
+    LGF_ERR_UNSUPPORTED_DIMS = 4, /* an extent or the plane sizes are outside what the FFT kernels take */
+    LGF_ERR_NOT_CONVERGED = 5,    /* max_iter updates applied before theta < tol */
+    LGF_ERR_NAN = 6,              /* theta or F became NaN or infinite */
+    LGF_ERR_TIMEOUT = 7,          /* the device loop hit its safety bound on body executions */
+    LGF_ERR_STATE = 8             /* call out of order (e.g. lgf_fix before lgf_set_links) */
+} lgf_status;
+
+/* creation flags */
+#define LGF_FP64 0        /* every step in FP64 */
+#define LGF_MIXED 1       /* FP32 Delta/FFT/update until theta < switch_tol, then FP64 (see lgf_set_switch_tol) */
+#define LGF_NO_GAUGE 2    /* do not accumulate G (lgf_get_gauge then fails); FP64 mode only */
+
+/*
+ * lgf_create: allocate a context for a lattice of extents dims[4].
+ * Each extent must be one of 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128 and the
+ * plane sizes must satisfy Lx*Ly <= 3072 and Lz*Lt <= 12288 (the FFT tiles are
+ * held in shared memory); else LGF_ERR_UNSUPPORTED_DIMS.  flags: LGF_FP64 or
+ * LGF_MIXED, optionally | LGF_NO_GAUGE.  *out receives the context.
+ */
+int lgf_create(const int dims[4], int flags, lgf_ctx** out);
+
+/* Run all later work of ctx on this cudaStream_t (NULL = legacy default stream). */
+int lgf_set_stream(lgf_ctx* ctx, void* cuda_stream);
+
+/*
+ * lgf_set_links: copy links U ([4][V][3][3] complex128, layout above) into the
+ * context, keeping rows 0,1 of each link (row 2 is rebuilt as conj(row0 x row1),
+ * the 12-real form).  Checks every link: max|U U^dag - 1| and |det U - 1| must
+ * be below 1e-12, else LGF_ERR_NOT_SU3 (the context keeps no links then).
+ * Resets the accumulated gauge transformation G to 1.
+ */
+int lgf_set_links(lgf_ctx* ctx, const double* U, int on_device);
+
+/*
+ * lgf_fix: iterate Fourier-accelerated steepest descent on the stored links
+ * until theta < theta_tol (tested on the current links before each update) or
+ * max_iter updates are applied.  alpha > 0 is the step (0.08 in the paper).
+ * Outputs (each may be NULL): *iters = updates applied, *F and *theta of the
+ * final links.  They are valid also when the call returns LGF_ERR_NOT_CONVERGED
+ * or LGF_ERR_NAN.  In LGF_MIXED mode the FP32 phase runs while theta >=
+ * switch_tol; then G is reprojected onto SU(3) in FP64 and the links are rebuilt
+ * as U = G U_in G^dag(x+mu) in FP64 before the FP64 phase.  Blocks until done.
+ */
+int lgf_fix(lgf_ctx* ctx, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta);
+
+/* lgf_get_links: write the current links, rows 0,1 as stored and row 2 rebuilt. */
+int lgf_get_links(lgf_ctx* ctx, double* U_out, int on_device);
+
+/*
+ * lgf_get_gauge: write the accumulated gauge transformation G ([V][3][3]
+ * complex128), so that the current links equal G(x) U_in(x) G^dag(x+mu) up to
+ * rounding.  LGF_ERR_STATE if the context was created with LGF_NO_GAUGE.
+ */
+int lgf_get_gauge(lgf_ctx* ctx, double* G_out, int on_device);
+
+/*
+ * lgf_get_history: copy (theta_n, F_n) of the last lgf_fix, n = 0..iters, as
+ * 2*n doubles into theta_F (host memory), at most n_max pairs; *written gets the
+ * number of pairs.  The device keeps the most recent 65536 pairs.
+ */
+int lgf_get_history(lgf_ctx* ctx, double* theta_F, int n_max, int* written);
+
+/* lgf_stats: phase split of the last lgf_fix (iterations in the FP32 phase). */
+int lgf_get_stats(lgf_ctx* ctx, int* iters_fp32, int* iters_fp64);
+
+/* Threshold on theta that ends the FP32 phase of LGF_MIXED (default 1e-6). */
+int lgf_set_switch_tol(lgf_ctx* ctx, double switch_tol);
+
+/*
+ * Stage entry points (same arithmetic as inside lgf_fix, exposed for checking
+ * each step on its own).  All arrays are caller-owned, layouts as above.
+ *
+ * lgf_delta: Delta ([V][3][3] complex128, may be NULL), theta and F of the
+ *   stored links, in FP64.
+ * lgf_accelerate: Delta~ = IFFT[p2max/p2 FFT[Delta]]/V of a given traceless
+ *   anti-Hermitian field Delta ([V][3][3]); Dt_out gets the full matrices.
+ * lgf_build_g: g = reunit(1 + alpha/2 Dt) of a given Dt ([V][3][3]).
+ */
+int lgf_delta(lgf_ctx* ctx, double* Delta_out, int on_device, double* theta, double* F);
+int lgf_accelerate(lgf_ctx* ctx, const double* Delta_in, double* Dt_out, int on_device);
+int lgf_build_g(lgf_ctx* ctx, const double* Dt_in, double alpha, double* g_out, int on_device);
+
+/*
+ * lgf_time_kernels (instrumentation): run n_iter iterations of the loop body on
+ * the stored links, launching the kernels one by one on the context's stream
+ * with CUDA events around each launch, and write to ms[4] the mean duration
+ * (milliseconds) of (0) the Delta + x,y FFT kernel, (1) the z,t FFT +
+ * accelerator kernel, (2) the inverse x,y FFT + g kernel, (3) the update
+ * kernel.  precision 64 times the FP64 kernels; 32 the FP32 kernels (mixed
+ * contexts only; they start from an FP32 copy of the stored links).  The stored
+ * links advance by n_iter updates (precision 64) or are left as they were (32).
+ */
+int lgf_time_kernels(lgf_ctx* ctx, double alpha, int n_iter, int precision, double* ms);
+
+/* Release all device memory of ctx.  NULL is a no-op. */
+void lgf_destroy(lgf_ctx* ctx);
+
+/* Static description of a status code. */
+const char* lgf_strerror(int status);
+
+/* Text of the last failed CUDA call on this thread (empty if none). */
+const char* lgf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGF_H */

@@ -1,0 +1,272 @@
+// Kernels around the iteration: conversion between the caller's
+// [..][3][3] complex128 arrays and the library's 12-real planes, the SU(3)
+// check of input links, stand-alone stage kernels, and the precision switch of
+// the mixed mode (FP32 phase -> FP64 phase).
+#pragma once
+#include "lgf_kernels.cuh"
+
+namespace lgf {
+
+__device__ __forceinline__ double dmax_nan(double a, double b)
+{
+    // NaN counts as larger than anything
+    if (!(a == a)) return a;
+    if (!(b == b)) return b;
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double v)
+{
+    if (!(v <= 1e300)) v = 1e300;  // NaN and inf compare as huge
+    // non-negative doubles order like their bit patterns
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// Interleaved [4][V][3][3] complex128 -> rows 0,1 planes of T; optional SU(3)
+// check of the full input matrix: err[0] = max |U U^dag - 1|, err[1] = max |det U - 1|.
+template <typename T>
+static __global__ void k_pack_links(int V, const double* __restrict__ in, vec2_t<T>* __restrict__ U,
+                             unsigned long long* err, int validate)
+{
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;  // link index mu*V + s
+    double e_unit = 0.0, e_det = 0.0;
+    if (idx < 4L * V) {
+        const int mu = (int)(idx / V), s = (int)(idx - (long)mu * V);
+        const double* p = in + idx * 18;
+        cx<double> m[9];
+#pragma unroll
+        for (int e = 0; e < 9; e++) m[e] = mk<double>(p[2 * e], p[2 * e + 1]);
+#pragma unroll
+        for (int e = 0; e < 6; e++) {
+            vec2_t<T> v;
+            v.x = (T)m[e].re;
+            v.y = (T)m[e].im;
+            U[(size_t)(mu * 6 + e) * V + s] = v;
+        }
+        if (validate) {
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    cx<double> acc = cmulc(m[3 * i], m[3 * j]);
+                    acc = cmacc(acc, m[3 * i + 1], m[3 * j + 1]);
+                    acc = cmacc(acc, m[3 * i + 2], m[3 * j + 2]);
+                    if (i == j) acc.re -= 1.0;
+                    e_unit = dmax_nan(e_unit, sqrt(norm2(acc)));
+                }
+            cx<double> r2[3];
+            complete_row2(m, r2);  // conj of the cofactor row: det = sum_j m2j conj(r2_j)
+            cx<double> det = cmulc(m[6], r2[0]);
+            det = cmacc(det, m[7], r2[1]);
+            det = cmacc(det, m[8], r2[2]);
+            det.re -= 1.0;
+            e_det = sqrt(norm2(det));
+            if (!(e_det == e_det)) e_det = 1e300;
+        }
+    }
+    if (validate) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            e_unit = dmax_nan(e_unit, __shfl_down_sync(0xffffffffu, e_unit, o));
+            e_det = dmax_nan(e_det, __shfl_down_sync(0xffffffffu, e_det, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomic_max_nonneg(err, e_unit);
+            atomic_max_nonneg(err + 1, e_det);
+        }
+    }
+}
+
+// rows 0,1 planes -> interleaved [nmat][V][3][3] complex128 with row 2 rebuilt
+template <typename T>
+static __global__ void k_unpack_su3(int V, int nmat, const vec2_t<T>* __restrict__ U, double* __restrict__ out)
+{
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nmat * V) return;
+    const int mu = (int)(idx / V), s = (int)(idx - (long)mu * V);
+    cx<T> m[9];
+#pragma unroll
+    for (int e = 0; e < 6; e++) m[e] = ld<T>(U + (size_t)(mu * 6 + e) * V + s);
+    complete_row2(m, m + 6);
+    double* p = out + idx * 18;
+#pragma unroll
+    for (int e = 0; e < 9; e++) {
+        p[2 * e] = (double)m[e].re;
+        p[2 * e + 1] = (double)m[e].im;
+    }
+}
+
+template <typename T> __global__ void k_identity_rows(int V, vec2_t<T>* __restrict__ G)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        vec2_t<T> v;
+        v.x = (e == 0 || e == 4) ? (T)1 : (T)0;
+        v.y = (T)0;
+        G[(size_t)e * V + s] = v;
+    }
+}
+
+// [V][3][3] traceless anti-Hermitian complex128 -> the four packed fields
+static __global__ void k_pack_delta(int V, const double* __restrict__ in, double2* __restrict__ Fd)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    const double* p = in + (size_t)s * 18;
+    Fd[s] = make_double2(p[2], p[3]);                 // Delta01
+    Fd[(size_t)V + s] = make_double2(p[4], p[5]);     // Delta02
+    Fd[(size_t)2 * V + s] = make_double2(p[10], p[11]);  // Delta12
+    Fd[(size_t)3 * V + s] = make_double2(p[1], p[9]);    // Im Delta00 + i Im Delta11
+}
+
+// the four packed fields -> [V][3][3] traceless anti-Hermitian complex128
+static __global__ void k_unpack_delta(int V, const double2* __restrict__ Fd, double* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    const double2 d01 = Fd[s], d02 = Fd[(size_t)V + s], d12 = Fd[(size_t)2 * V + s], ab = Fd[(size_t)3 * V + s];
+    double* p = out + (size_t)s * 18;
+    const double m[18] = {0.0, ab.x, d01.x, d01.y, d02.x, d02.y, -d01.x, d01.y, 0.0, ab.y,
+                          d12.x, d12.y, -d02.x, d02.y, -d12.x, d12.y, 0.0, -(ab.x + ab.y)};
+#pragma unroll
+    for (int e = 0; e < 18; e++) p[e] = m[e];
+}
+
+// [9][V] planes of full matrices -> [V][3][3] complex128
+static __global__ void k_unpack_full(int V, const double2* __restrict__ g, double* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    double* p = out + (size_t)s * 18;
+#pragma unroll
+    for (int e = 0; e < 9; e++) {
+        const double2 v = g[(size_t)e * V + s];
+        p[2 * e] = v.x;
+        p[2 * e + 1] = v.y;
+    }
+}
+
+// plane-wise FFT along x and y of the four fields (stand-alone stage)
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kMaxThreads) k_xy_fft(Lat d, const XyFft F, vec2_t<T>* __restrict__ Fd,
+                                                        const vec2_t<T>* __restrict__ twx,
+                                                        const vec2_t<T>* __restrict__ twy)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    const int P = d.P, V = d.V, s0 = blockIdx.x * P;
+    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+        const int f = i / P, xy = i - f * P;
+        sm[i] = Fd[(size_t)f * V + s0 + xy];
+    }
+    __syncthreads();
+    fft_xy_fields<T>(F, P, sm, sm + 4 * P, twx, twy, INV ? kInv : kFwd);
+    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+        const int f = i / P, xy = i - f * P;
+        Fd[(size_t)f * V + s0 + xy] = sm[i];
+    }
+}
+
+// ---------------------------------------------------------------- mixed mode
+
+// start of the FP32 phase: FP32 copy of the current FP64 links, G32 = 1
+static __global__ void k_mixed_prep(int V, const double2* __restrict__ U64, float2* __restrict__ U32,
+                             float2* __restrict__ G32, const Ctl* ctl)
+{
+    if (ld_flag(&ctl->done)) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+#pragma unroll
+    for (int e = 0; e < 24; e++) {
+        const double2 v = U64[(size_t)e * V + s];
+        U32[(size_t)e * V + s] = make_float2((float)v.x, (float)v.y);
+    }
+#pragma unroll
+    for (int e = 0; e < 6; e++) G32[(size_t)e * V + s] = make_float2((e == 0 || e == 4) ? 1.f : 0.f, 0.f);
+}
+
+// end of the FP32 phase: Gs = reunit(G32) in FP64, stored as full 3x3 planes
+static __global__ void k_switch_gs(int V, const float2* __restrict__ G32, double2* __restrict__ Gs, const Ctl* ctl)
+{
+    if (ld_flag(&ctl->done)) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    cx<double> X[6], g[9];
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        const float2 v = G32[(size_t)e * V + s];
+        X[e] = mk<double>((double)v.x, (double)v.y);
+    }
+    reunit_rows(X, g);
+#pragma unroll
+    for (int e = 0; e < 9; e++) Gs[(size_t)e * V + s] = make_double2(g[e].re, g[e].im);
+}
+
+// U_mu(x) <- Gs(x) U_mu(x) Gs^dag(x+mu) and G(x) <- Gs(x) G(x), FP64, in place
+static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restrict__ U, double2* __restrict__ G,
+                                                const double2* __restrict__ Gs, const Ctl* ctl)
+{
+    if (ld_flag(&ctl->done)) return;
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    int c[4];
+    site_coords(d, s, c);
+    cx<double> gx[9];
+    load_g<double>(Gs, V, s, gx);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        cx<double> u[9];
+        load_link<double>(U, V, mu, s, u);
+        cx<double> A[6];
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<double> acc = cmul(gx[3 * i], u[j]);
+                acc = cmac(acc, gx[3 * i + 1], u[3 + j]);
+                acc = cmac(acc, gx[3 * i + 2], u[6 + j]);
+                A[3 * i + j] = acc;
+            }
+        cx<double> gn[9];
+        load_g<double>(Gs, V, site_shift(d, s, c[mu], mu, +1), gn);
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<double> acc = cmulc(A[3 * i], gn[3 * j]);
+                acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
+                acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
+                st<double>(U + (size_t)(mu * 6 + 3 * i + j) * V + s, acc);
+            }
+    }
+    if (G != nullptr) {
+        cx<double> Gm[9];
+#pragma unroll
+        for (int e = 0; e < 6; e++) Gm[e] = ldv<double>(G + (size_t)e * V + s);
+        complete_row2(Gm, Gm + 6);
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<double> acc = cmul(gx[3 * i], Gm[j]);
+                acc = cmac(acc, gx[3 * i + 1], Gm[3 + j]);
+                acc = cmac(acc, gx[3 * i + 2], Gm[6 + j]);
+                st<double>(G + (size_t)(3 * i + j) * V + s, acc);
+            }
+    }
+}
+
+// hand over from the FP32 phase to the FP64 phase
+static __global__ void k_phase_switch(Ctl* ctl)
+{
+    if (ld_flag(&ctl->done)) return;
+    ctl->phase = 1;
+    ctl->tol = ctl->tol_final;
+    ctl->phase_done = 0;
+    ctl->body_runs = 0u;
+}
+
+}  // namespace lgf

@@ -1,0 +1,680 @@
+// C ABI of the gauge-fixing library (declarations and contracts in include/lgf.h).
+//
+// Host side: context and device memory, twiddle and momentum tables, kernel
+// configuration, and the device-resident loop.  One lgf_fix is one CUDA graph
+// launch: the iteration body sits in a conditional WHILE node whose condition
+// the last kernel of the body sets from the device loop state, so the loop runs
+// to convergence with no host round trip.  The mixed mode chains an FP32 loop,
+// the FP64 re-projection and an FP64 loop inside the same graph.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lgf.h"
+#include "lgf_launch.h"
+
+using namespace lgf;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+void set_error(const char* what, cudaError_t e, const char* file, int line)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) {                               \
+            set_error(#call, e_, __FILE__, __LINE__);          \
+            return LGF_ERR_CUDA;                               \
+        }                                                      \
+    } while (0)
+
+#define CKR(call)                        \
+    do {                                 \
+        int r_ = (call);                 \
+        if (r_ != LGF_OK) return r_;     \
+    } while (0)
+
+constexpr int kHistCap = 65536;
+
+bool length_ok(int L)
+{
+    return L == 4 || L == 6 || L == 8 || L == 12 || L == 16 || L == 24 || L == 32 || L == 48 || L == 64 ||
+           L == 96 || L == 128;
+}
+
+}  // namespace
+
+struct lgf_ctx {
+    int L[4] = {0, 0, 0, 0};
+    int V = 0;
+    int flags = 0;
+    bool mixed = false, track = true;
+    cudaStream_t stream = nullptr;   // user stream for launches
+    cudaStream_t cap = nullptr;      // private stream used to capture graphs
+    Lat lat{};
+    Shape sh64{}, sh32{};
+    Tables tb{};
+    // state
+    double2* U64 = nullptr;
+    double2* G64 = nullptr;
+    double2* g64 = nullptr;   // [9][V]; also the FP64 reprojection of G at the precision switch
+    float2* U32 = nullptr;
+    float2* G32 = nullptr;
+    float2* g32 = nullptr;
+    void* Fd = nullptr;       // [4][V] double2 (the FP32 phase uses the front half as float2)
+    double* partials = nullptr;
+    Ctl* ctl = nullptr;       // loop state of lgf_fix
+    Ctl* ctl_stage = nullptr; // state used by the stage entry points
+    double2* hist = nullptr;
+    unsigned long long* err = nullptr;
+    double* stage = nullptr;  // device staging for host arrays
+    size_t stage_bytes = 0;
+    void* tables = nullptr;
+    Ctl* host_ctl = nullptr;  // pinned
+    bool have_links = false;
+    double switch_tol = 1e-6;
+    cudaGraphExec_t exec = nullptr;
+    int last_iters = 0, last_iters32 = 0, last_hist = 0;
+};
+
+namespace {
+
+// Shared-memory FFT tiles: an xy-plane of all four fields plus a scratch of
+// nfc fields, and two buffers of a pencil of xw x-columns over (z, t).
+bool pick_shape(const Lat& d, size_t elem, int prefer_nfc, int prefer_xw, Shape* sh)
+{
+    const size_t budget = 220 * 1024;
+    const int P = d.P;
+    int nfc = prefer_nfc;
+    while (nfc > 1 && (size_t)(4 + nfc) * P * elem > budget) nfc >>= 1;
+    if ((size_t)(4 + nfc) * P * elem > budget) return false;
+    const int ZT = d.L[2] * d.L[3];
+    int xw = prefer_xw;
+    while (xw > 1 && (d.L[0] % xw || (size_t)2 * xw * ZT * elem > budget)) xw >>= 1;
+    if ((size_t)2 * xw * ZT * elem > budget) return false;
+    sh->nt_xy = 512;
+    sh->nt_zt = 512;
+    XyFft& X = sh->xy;
+    X.px = make_axis_plan(d.L[0]);
+    X.py = make_axis_plan(d.L[1]);
+    X.mx = make_linemap(1u << 30, 0, (unsigned)d.L[0], 1);
+    X.my = make_linemap((unsigned)d.L[0], (unsigned)P, 1, (unsigned)d.L[0]);
+    X.lx = make_lines((unsigned)(nfc * d.L[1]));
+    X.ly = make_lines((unsigned)(nfc * d.L[0]));
+    X.nfc = nfc;
+    ZtFft& Z = sh->zt;
+    Z.pz = make_axis_plan(d.L[2]);
+    Z.pt = make_axis_plan(d.L[3]);
+    Z.mz = make_linemap((unsigned)xw, (unsigned)(d.L[2] * xw), 1, (unsigned)xw);
+    Z.mt = make_linemap(1u << 30, 0, 1, (unsigned)(d.L[2] * xw));
+    Z.lz = make_lines((unsigned)(xw * d.L[3]));
+    Z.lt = make_lines((unsigned)(xw * d.L[2]));
+    Z.xw = xw;
+    return true;
+}
+
+template <typename T> const Shape& shape_of(const lgf_ctx* c);
+template <> const Shape& shape_of<double>(const lgf_ctx* c) { return c->sh64; }
+template <> const Shape& shape_of<float>(const lgf_ctx* c) { return c->sh32; }
+
+// one iteration after Delta: FFT(z,t)+scale+IFFT(t,z), IFFT(x,y)+g, update, Delta+FFT(x,y)
+template <typename T>
+void launch_body(lgf_ctx* c, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, vec2_t<T>* g)
+{
+    vec2_t<T>* Fd = reinterpret_cast<vec2_t<T>*>(c->Fd);
+    const Shape& sh = shape_of<T>(c);
+    launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl);
+    launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g, c->ctl);
+    launch_update<T>(c->lat, s, U, G, g, c->ctl);
+    launch_delta<T>(c->lat, sh, c->tb, s, U, Fd, c->partials, c->ctl, c->hist, true);
+}
+
+// ---------------------------------------------------------------- graph
+
+int capture_begin(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps)
+{
+    CK(cudaStreamBeginCaptureToGraph(c->cap, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                     cudaStreamCaptureModeThreadLocal));
+    return LGF_OK;
+}
+
+int capture_end(lgf_ctx* c, std::vector<cudaGraphNode_t>& deps)
+{
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    CK(cudaGetLastError());
+    CK(cudaStreamGetCaptureInfo(c->cap, &st, nullptr, nullptr, &d, nullptr, &nd));
+    deps.assign(d, d + nd);
+    cudaGraph_t out;
+    CK(cudaStreamEndCapture(c->cap, &out));
+    return LGF_OK;
+}
+
+// adds a WHILE node after deps; *body receives its body graph, *h its handle
+int add_while(cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, cudaGraph_t* body, cudaGraphConditionalHandle* h)
+{
+    CK(cudaGraphConditionalHandleCreate(h, graph, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = *h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p));
+    *body = p.conditional.phGraph_out[0];
+    deps.assign(1, node);
+    return LGF_OK;
+}
+
+template <typename T>
+int add_loop(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, vec2_t<T>* U, vec2_t<T>* G,
+             vec2_t<T>* g)
+{
+    cudaGraph_t body;
+    cudaGraphConditionalHandle h;
+    CKR(add_while(graph, deps, &body, &h));
+    CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_body<T>(c, c->cap, U, G, g);
+    launch_loop_ctl(c->cap, c->ctl, h);
+    CK(cudaGetLastError());
+    cudaGraph_t out;
+    CK(cudaStreamEndCapture(c->cap, &out));
+    return LGF_OK;
+}
+
+int build_graph(lgf_ctx* c)
+{
+    if (c->exec) return LGF_OK;
+    cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    std::vector<cudaGraphNode_t> deps;
+    double2* Fd64 = reinterpret_cast<double2*>(c->Fd);
+    if (c->mixed) {
+        CKR(capture_begin(c, graph, deps));
+        launch_mixed_prep(c->cap, c->V, c->U64, c->U32, c->G32, c->ctl);
+        launch_delta<float>(c->lat, c->sh32, c->tb, c->cap, c->U32, reinterpret_cast<float2*>(c->Fd), c->partials,
+                            c->ctl, c->hist, true);
+        CKR(capture_end(c, deps));
+        CKR(add_loop<float>(c, graph, deps, c->U32, c->G32, c->g32));
+        CKR(capture_begin(c, graph, deps));
+        launch_switch(c->cap, c->lat, c->G32, c->g64, c->U64, c->G64, c->ctl);
+        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->U64, Fd64, c->partials, c->ctl, c->hist, true);
+        CKR(capture_end(c, deps));
+        CKR(add_loop<double>(c, graph, deps, c->U64, c->G64, c->g64));
+    } else {
+        CKR(capture_begin(c, graph, deps));
+        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->U64, Fd64, c->partials, c->ctl, c->hist, true);
+        CKR(capture_end(c, deps));
+        CKR(add_loop<double>(c, graph, deps, c->U64, c->track ? c->G64 : nullptr, c->g64));
+    }
+    cudaError_t e = cudaGraphInstantiate(&c->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        set_error("cudaGraphInstantiate", e, __FILE__, __LINE__);
+        c->exec = nullptr;
+        return LGF_ERR_CUDA;
+    }
+    return LGF_OK;
+}
+
+// ---------------------------------------------------------------- set-up
+
+int alloc(void** p, size_t bytes)
+{
+    CK(cudaMalloc(p, bytes));
+    return LGF_OK;
+}
+
+int ensure_stage(lgf_ctx* c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes) return LGF_OK;
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    CKR(alloc((void**)&c->stage, bytes));
+    c->stage_bytes = bytes;
+    return LGF_OK;
+}
+
+int build_tables(lgf_ctx* c)
+{
+    size_t n = 0;
+    for (int mu = 0; mu < 4; mu++) n += c->L[mu];
+    const size_t bytes = n * (sizeof(double2) + sizeof(float2) + sizeof(double));
+    CKR(alloc(&c->tables, bytes));
+    std::vector<unsigned char> h(bytes);
+    double2* t64 = reinterpret_cast<double2*>(h.data());
+    float2* t32 = reinterpret_cast<float2*>(h.data() + n * sizeof(double2));
+    double* s2 = reinterpret_cast<double*>(h.data() + n * (sizeof(double2) + sizeof(float2)));
+    const double two_pi = 6.283185307179586476925286766559;
+    const double pi = 3.14159265358979323846264338327950;
+    size_t off = 0;
+    c->tb.p2max = 0;
+    for (int mu = 0; mu < 4; mu++) {
+        const int L = c->L[mu];
+        double mx = 0;
+        for (int m = 0; m < L; m++) {
+            const double a = two_pi * m / L;
+            t64[off + m] = make_double2(cos(a), -sin(a));  // exp(-2 pi i m / L)
+            t32[off + m] = make_float2((float)cos(a), (float)-sin(a));
+            const double sv = sin(pi * m / L);
+            s2[off + m] = 4.0 * sv * sv;
+            if (s2[off + m] > mx) mx = s2[off + m];
+        }
+        c->tb.p2max += mx;
+        unsigned char* base = reinterpret_cast<unsigned char*>(c->tables);
+        c->tb.tw64[mu] = reinterpret_cast<const double2*>(base) + off;
+        c->tb.tw32[mu] = reinterpret_cast<const float2*>(base + n * sizeof(double2)) + off;
+        c->tb.s2[mu] = reinterpret_cast<const double*>(base + n * (sizeof(double2) + sizeof(float2))) + off;
+        off += L;
+    }
+    CK(cudaMemcpy(c->tables, h.data(), bytes, cudaMemcpyHostToDevice));
+    return LGF_OK;
+}
+
+int create_impl(const int dims[4], int flags, lgf_ctx* c)
+{
+    for (int mu = 0; mu < 4; mu++) {
+        if (!length_ok(dims[mu])) return LGF_ERR_UNSUPPORTED_DIMS;
+        c->L[mu] = dims[mu];
+    }
+    const long V = (long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V * 24 > 0x7fffffffL) return LGF_ERR_UNSUPPORTED_DIMS;  // plane offsets are 32-bit
+    c->V = (int)V;
+    c->flags = flags;
+    c->mixed = (flags & LGF_MIXED) != 0;
+    c->track = c->mixed || !(flags & LGF_NO_GAUGE);
+    Lat& d = c->lat;
+    int st = 1;
+    for (int mu = 0; mu < 4; mu++) {
+        d.L[mu] = dims[mu];
+        d.stride[mu] = st;
+        st *= dims[mu];
+    }
+    d.V = c->V;
+    d.P = dims[0] * dims[1];
+    d.nplanes = dims[2] * dims[3];
+    if (!pick_shape(d, sizeof(double2), 2, 4, &c->sh64)) return LGF_ERR_UNSUPPORTED_DIMS;
+    if (!pick_shape(d, sizeof(float2), 2, 8, &c->sh32)) return LGF_ERR_UNSUPPORTED_DIMS;
+
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (ndev < 1) return LGF_ERR_CUDA;
+    CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CK(prepare_kernels<double>(d, c->sh64));
+    if (c->mixed) CK(prepare_kernels<float>(d, c->sh32));
+
+    const size_t Vs = (size_t)c->V;
+    CKR(alloc((void**)&c->U64, 24 * Vs * sizeof(double2)));
+    if (c->track) CKR(alloc((void**)&c->G64, 6 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->g64, 9 * Vs * sizeof(double2)));
+    CKR(alloc(&c->Fd, 4 * Vs * sizeof(double2)));
+    if (c->mixed) {
+        CKR(alloc((void**)&c->U32, 24 * Vs * sizeof(float2)));
+        CKR(alloc((void**)&c->G32, 6 * Vs * sizeof(float2)));
+        CKR(alloc((void**)&c->g32, 9 * Vs * sizeof(float2)));
+    }
+    CKR(alloc((void**)&c->partials, 2 * (size_t)d.nplanes * sizeof(double)));
+    CKR(alloc((void**)&c->ctl, sizeof(Ctl)));
+    CKR(alloc((void**)&c->ctl_stage, sizeof(Ctl)));
+    CKR(alloc((void**)&c->hist, kHistCap * sizeof(double2)));
+    CKR(alloc((void**)&c->err, 2 * sizeof(unsigned long long)));
+    CK(cudaMemset(c->ctl, 0, sizeof(Ctl)));
+    CK(cudaMemset(c->ctl_stage, 0, sizeof(Ctl)));
+    CK(cudaMallocHost((void**)&c->host_ctl, sizeof(Ctl)));
+    CKR(build_tables(c));
+    return LGF_OK;
+}
+
+void free_all(lgf_ctx* c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
+                    c->hist, c->err, c->stage, c->tables};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->host_ctl) cudaFreeHost(c->host_ctl);
+    if (c->cap) cudaStreamDestroy(c->cap);
+}
+
+// copy a caller array to device memory (or use it in place) and return the device pointer
+int stage_in(lgf_ctx* c, const double* p, size_t bytes, int on_device, const double** out)
+{
+    if (on_device) {
+        *out = p;
+        return LGF_OK;
+    }
+    CKR(ensure_stage(c, bytes));
+    CK(cudaMemcpyAsync(c->stage, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    *out = c->stage;
+    return LGF_OK;
+}
+
+int stage_out_begin(lgf_ctx* c, double* p, size_t bytes, int on_device, double** dev)
+{
+    if (on_device) {
+        *dev = p;
+        return LGF_OK;
+    }
+    CKR(ensure_stage(c, bytes));
+    *dev = c->stage;
+    return LGF_OK;
+}
+
+int stage_out_end(lgf_ctx* c, double* p, size_t bytes, int on_device)
+{
+    if (!on_device) CK(cudaMemcpyAsync(p, c->stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    return LGF_OK;
+}
+
+int reset_stage_ctl(lgf_ctx* c, double alpha = 0.0)
+{
+    Ctl h;
+    memset(&h, 0, sizeof h);
+    h.alpha = alpha;
+    h.tol = -1.0;
+    h.tol_final = -1.0;
+    h.max_iter = 0x7fffffff;
+    h.phase = 1;
+    *c->host_ctl = h;
+    CK(cudaMemcpyAsync(c->ctl_stage, c->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+    return LGF_OK;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+
+extern "C" {
+
+const char* lgf_strerror(int status)
+{
+    switch (status) {
+    case LGF_OK: return "ok";
+    case LGF_ERR_ARG: return "invalid argument";
+    case LGF_ERR_CUDA: return "CUDA error";
+    case LGF_ERR_NOT_SU3: return "input links are not SU(3) to 1e-12";
+    case LGF_ERR_UNSUPPORTED_DIMS: return "unsupported lattice extents";
+    case LGF_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case LGF_ERR_NAN: return "theta or F became NaN or infinite";
+    case LGF_ERR_TIMEOUT: return "device loop hit its safety bound";
+    case LGF_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+const char* lgf_last_error(void) { return g_last_error; }
+
+int lgf_create(const int dims[4], int flags, lgf_ctx** out)
+{
+    if (!dims || !out) return LGF_ERR_ARG;
+    *out = nullptr;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE)) return LGF_ERR_ARG;
+    lgf_ctx* c = new (std::nothrow) lgf_ctx();
+    if (!c) return LGF_ERR_ARG;
+    int r = create_impl(dims, flags, c);
+    if (r != LGF_OK) {
+        free_all(c);
+        delete c;
+        return r;
+    }
+    *out = c;
+    return LGF_OK;
+}
+
+void lgf_destroy(lgf_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+int lgf_set_stream(lgf_ctx* c, void* stream)
+{
+    if (!c) return LGF_ERR_ARG;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    return LGF_OK;
+}
+
+int lgf_set_switch_tol(lgf_ctx* c, double tol)
+{
+    if (!c || !(tol > 0)) return LGF_ERR_ARG;
+    c->switch_tol = tol;
+    return LGF_OK;
+}
+
+int lgf_set_links(lgf_ctx* c, const double* U, int on_device)
+{
+    if (!c || !U) return LGF_ERR_ARG;
+    const size_t bytes = (size_t)4 * c->V * 18 * sizeof(double);
+    const double* src;
+    c->have_links = false;
+    CKR(stage_in(c, U, bytes, on_device, &src));
+    CK(cudaMemsetAsync(c->err, 0, 2 * sizeof(unsigned long long), c->stream));
+    launch_pack_links64(c->stream, c->V, src, c->U64, c->err);
+    if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
+    CK(cudaGetLastError());
+    unsigned long long e[2];
+    CK(cudaMemcpyAsync(e, c->err, sizeof e, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double eu, ed;
+    memcpy(&eu, &e[0], sizeof eu);
+    memcpy(&ed, &e[1], sizeof ed);
+    if (!(eu < 1e-12) || !(ed < 1e-12)) return LGF_ERR_NOT_SU3;
+    c->have_links = true;
+    return LGF_OK;
+}
+
+int lgf_fix(lgf_ctx* c, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta)
+{
+    if (!c) return LGF_ERR_ARG;
+    if (!(alpha > 0) || !(theta_tol >= 0) || max_iter < 0) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(build_graph(c));
+    Ctl h;
+    memset(&h, 0, sizeof h);
+    h.tol_final = theta_tol;
+    h.tol = c->mixed ? (c->switch_tol > theta_tol ? c->switch_tol : theta_tol) : theta_tol;
+    h.alpha = alpha;
+    h.max_iter = max_iter;
+    h.phase = c->mixed ? 0 : 1;
+    h.hist_cap = kHistCap;
+    *c->host_ctl = h;
+    CK(cudaMemcpyAsync(c->ctl, c->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaGraphLaunch(c->exec, c->stream));
+    CK(cudaMemcpyAsync(c->host_ctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    const Ctl r = *c->host_ctl;
+    c->last_iters = r.iter;
+    c->last_iters32 = r.iter_phase0;
+    c->last_hist = r.iter + 1;
+    if (iters) *iters = r.iter;
+    if (F) *F = r.F;
+    if (theta) *theta = r.theta;
+    if (r.nan_seen) return LGF_ERR_NAN;
+    if (r.converged) return LGF_OK;
+    if (!r.done) return LGF_ERR_TIMEOUT;
+    return LGF_ERR_NOT_CONVERGED;
+}
+
+int lgf_get_links(lgf_ctx* c, double* U_out, int on_device)
+{
+    if (!c || !U_out) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    const size_t bytes = (size_t)4 * c->V * 18 * sizeof(double);
+    double* dst;
+    CKR(stage_out_begin(c, U_out, bytes, on_device, &dst));
+    launch_unpack_su3_64(c->stream, c->V, 4, c->U64, dst);
+    CK(cudaGetLastError());
+    return stage_out_end(c, U_out, bytes, on_device);
+}
+
+int lgf_get_gauge(lgf_ctx* c, double* G_out, int on_device)
+{
+    if (!c || !G_out) return LGF_ERR_ARG;
+    if (!c->track) return LGF_ERR_STATE;
+    if (!c->have_links) return LGF_ERR_STATE;
+    const size_t bytes = (size_t)c->V * 18 * sizeof(double);
+    double* dst;
+    CKR(stage_out_begin(c, G_out, bytes, on_device, &dst));
+    launch_unpack_su3_64(c->stream, c->V, 1, c->G64, dst);
+    CK(cudaGetLastError());
+    return stage_out_end(c, G_out, bytes, on_device);
+}
+
+int lgf_get_history(lgf_ctx* c, double* theta_F, int n_max, int* written)
+{
+    if (!c || !theta_F || n_max < 0) return LGF_ERR_ARG;
+    int n = c->last_hist < kHistCap ? c->last_hist : kHistCap;
+    if (n > n_max) n = n_max;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(theta_F, c->hist, (size_t)n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (written) *written = n;
+    return LGF_OK;
+}
+
+int lgf_get_stats(lgf_ctx* c, int* iters_fp32, int* iters_fp64)
+{
+    if (!c) return LGF_ERR_ARG;
+    if (iters_fp32) *iters_fp32 = c->last_iters32;
+    if (iters_fp64) *iters_fp64 = c->last_iters - c->last_iters32;
+    return LGF_OK;
+}
+
+int lgf_delta(lgf_ctx* c, double* Delta_out, int on_device, double* theta, double* F)
+{
+    if (!c) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(reset_stage_ctl(c));
+    double2* Fd = reinterpret_cast<double2*>(c->Fd);
+    launch_delta<double>(c->lat, c->sh64, c->tb, c->stream, c->U64, Fd, c->partials, c->ctl_stage, nullptr, false);
+    CK(cudaGetLastError());
+    if (Delta_out) {
+        const size_t bytes = (size_t)c->V * 18 * sizeof(double);
+        double* dst;
+        CKR(stage_out_begin(c, Delta_out, bytes, on_device, &dst));
+        launch_unpack_delta(c->stream, c->V, Fd, dst);
+        CK(cudaGetLastError());
+        CKR(stage_out_end(c, Delta_out, bytes, on_device));
+    }
+    CK(cudaMemcpyAsync(c->host_ctl, c->ctl_stage, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (theta) *theta = c->host_ctl->theta;
+    if (F) *F = c->host_ctl->F;
+    return LGF_OK;
+}
+
+int lgf_accelerate(lgf_ctx* c, const double* Delta_in, double* Dt_out, int on_device)
+{
+    if (!c || !Delta_in || !Dt_out) return LGF_ERR_ARG;
+    const size_t bytes = (size_t)c->V * 18 * sizeof(double);
+    const double* src;
+    CKR(reset_stage_ctl(c));
+    CKR(stage_in(c, Delta_in, bytes, on_device, &src));
+    double2* Fd = reinterpret_cast<double2*>(c->Fd);
+    launch_pack_delta(c->stream, c->V, src, Fd);
+    launch_xy_fft<double>(c->lat, c->sh64, c->tb, c->stream, Fd, false);
+    launch_zt<double>(c->lat, c->sh64, c->tb, c->stream, Fd, c->ctl_stage);
+    launch_xy_fft<double>(c->lat, c->sh64, c->tb, c->stream, Fd, true);
+    CK(cudaGetLastError());
+    double* dst;
+    CKR(stage_out_begin(c, Dt_out, bytes, on_device, &dst));
+    launch_unpack_delta(c->stream, c->V, Fd, dst);
+    CK(cudaGetLastError());
+    return stage_out_end(c, Dt_out, bytes, on_device);
+}
+
+int lgf_build_g(lgf_ctx* c, const double* Dt_in, double alpha, double* g_out, int on_device)
+{
+    if (!c || !Dt_in || !g_out) return LGF_ERR_ARG;
+    const size_t bytes = (size_t)c->V * 18 * sizeof(double);
+    const double* src;
+    // the forward x,y FFT below and the builder's inverse are both unnormalised, so the
+    // builder sees Lx*Ly times the field: compensate in alpha, whose only use there is
+    // the factor alpha/2 on the field
+    CKR(reset_stage_ctl(c, alpha / (double)c->lat.P));
+    CKR(stage_in(c, Dt_in, bytes, on_device, &src));
+    double2* Fd = reinterpret_cast<double2*>(c->Fd);
+    launch_pack_delta(c->stream, c->V, src, Fd);
+    // the builder takes fields transformed along x and y: transform, then let it invert
+    launch_xy_fft<double>(c->lat, c->sh64, c->tb, c->stream, Fd, false);
+    launch_xyinv_g<double>(c->lat, c->sh64, c->tb, c->stream, Fd, c->g64, c->ctl_stage);
+    CK(cudaGetLastError());
+    double* dst;
+    CKR(stage_out_begin(c, g_out, bytes, on_device, &dst));
+    launch_unpack_full(c->stream, c->V, c->g64, dst);
+    CK(cudaGetLastError());
+    return stage_out_end(c, g_out, bytes, on_device);
+}
+
+int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double* ms)
+{
+    if (!c || !ms || n_iter < 1 || !(alpha > 0)) return LGF_ERR_ARG;
+    if (precision != 64 && precision != 32) return LGF_ERR_ARG;
+    if (precision == 32 && !c->mixed) return LGF_ERR_STATE;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(reset_stage_ctl(c, alpha));
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; i++) CK(cudaEventCreate(&ev[i]));
+    double acc[4] = {0, 0, 0, 0};
+    cudaStream_t s = c->stream;
+    int rc = LGF_OK;
+    if (precision == 32) launch_mixed_prep(s, c->V, c->U64, c->U32, c->G32, c->ctl_stage);
+    for (int it = 0; it < n_iter && rc == LGF_OK; it++) {
+        cudaEventRecord(ev[0], s);
+        if (precision == 64) {
+            double2* Fd = reinterpret_cast<double2*>(c->Fd);
+            launch_delta<double>(c->lat, c->sh64, c->tb, s, c->U64, Fd, c->partials, c->ctl_stage, nullptr, true);
+            cudaEventRecord(ev[1], s);
+            launch_zt<double>(c->lat, c->sh64, c->tb, s, Fd, c->ctl_stage);
+            cudaEventRecord(ev[2], s);
+            launch_xyinv_g<double>(c->lat, c->sh64, c->tb, s, Fd, c->g64, c->ctl_stage);
+            cudaEventRecord(ev[3], s);
+            launch_update<double>(c->lat, s, c->U64, c->track ? c->G64 : nullptr, c->g64, c->ctl_stage);
+        } else {
+            float2* Fd = reinterpret_cast<float2*>(c->Fd);
+            launch_delta<float>(c->lat, c->sh32, c->tb, s, c->U32, Fd, c->partials, c->ctl_stage, nullptr, true);
+            cudaEventRecord(ev[1], s);
+            launch_zt<float>(c->lat, c->sh32, c->tb, s, Fd, c->ctl_stage);
+            cudaEventRecord(ev[2], s);
+            launch_xyinv_g<float>(c->lat, c->sh32, c->tb, s, Fd, c->g32, c->ctl_stage);
+            cudaEventRecord(ev[3], s);
+            launch_update<float>(c->lat, s, c->U32, c->G32, c->g32, c->ctl_stage);
+        }
+        cudaEventRecord(ev[4], s);
+        cudaError_t e = cudaEventSynchronize(ev[4]);
+        if (e != cudaSuccess) {
+            set_error("cudaEventSynchronize", e, __FILE__, __LINE__);
+            rc = LGF_ERR_CUDA;
+            break;
+        }
+        for (int k = 0; k < 4; k++) {
+            float t = 0;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (int i = 0; i < 5; i++) cudaEventDestroy(ev[i]);
+    if (rc != LGF_OK) return rc;
+    CK(cudaGetLastError());
+    for (int k = 0; k < 4; k++) ms[k] = acc[k] / n_iter;
+    return LGF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// Shared device-side definitions of the CUDA gauge-fixing library: complex
+// arithmetic in registers, SU(3) helpers on the 12-real representation, the
+// lattice descriptor and the loop-control block.
+//
+// Method: Fourier-accelerated steepest descent for Landau gauge, arXiv:1301.3460
+// (functional in the introduction; alpha = 0.08 and theta < 1e-15 in the
+// description of the 32^4 runs; 12-real link storage named in the GPU set-up).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lgf {
+
+// ---------------------------------------------------------------- complex
+
+template <typename T> struct vec2;
+template <> struct vec2<double> { using type = double2; };
+template <> struct vec2<float> { using type = float2; };
+template <typename T> using vec2_t = typename vec2<T>::type;
+
+template <typename T> struct cx {
+    T re, im;
+};
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { return cx<T>{r, i}; }
+template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, T s) { return {a.re * s, a.im * s}; }
+template <typename T> __device__ __forceinline__ cx<T> conjg(cx<T> a) { return {a.re, -a.im}; }
+// a * b
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
+{
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b)
+{
+    return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -a.re * b.im)};
+}
+// acc + a * b
+template <typename T> __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+    return acc;
+}
+// acc + a * conj(b)
+template <typename T> __device__ __forceinline__ cx<T> cmacc(cx<T> acc, cx<T> a, cx<T> b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.im, b.re, acc.im);
+    acc.im = fma(-a.re, b.im, acc.im);
+    return acc;
+}
+// -i * a and +i * a
+template <typename T> __device__ __forceinline__ cx<T> mul_mi(cx<T> a) { return {a.im, -a.re}; }
+template <typename T> __device__ __forceinline__ cx<T> mul_pi(cx<T> a) { return {-a.im, a.re}; }
+template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return fma(a.re, a.re, a.im * a.im); }
+
+template <typename T> __device__ __forceinline__ cx<T> ld(const vec2_t<T>* p)
+{
+    vec2_t<T> v = __ldg(p);
+    return {v.x, v.y};
+}
+template <typename T> __device__ __forceinline__ cx<T> ldv(const vec2_t<T>* p)  // plain load (data written this launch)
+{
+    vec2_t<T> v = *p;
+    return {v.x, v.y};
+}
+template <typename T> __device__ __forceinline__ void st(vec2_t<T>* p, cx<T> a)
+{
+    vec2_t<T> v;
+    v.x = a.re;
+    v.y = a.im;
+    *p = v;
+}
+
+// ---------------------------------------------------------------- SU(3)
+
+// conj(a b - c d) with four fused multiply-adds per component
+template <typename T> __device__ __forceinline__ cx<T> cdet2c(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
+{
+    T re = a.re * b.re;
+    re = fma(-a.im, b.im, re);
+    re = fma(-c.re, d.re, re);
+    re = fma(c.im, d.im, re);
+    T im = -a.re * b.im;
+    im = fma(-a.im, b.re, im);
+    im = fma(c.re, d.im, im);
+    im = fma(c.im, d.re, im);
+    return {re, im};
+}
+
+// third row of an SU(3) matrix from its first two (m[0..2] row 0, m[3..5] row 1):
+// r2 = conj(r0 x r1)
+template <typename T> __device__ __forceinline__ void complete_row2(const cx<T>* m, cx<T>* r2)
+{
+    r2[0] = cdet2c(m[1], m[5], m[2], m[4]);
+    r2[1] = cdet2c(m[2], m[3], m[0], m[5]);
+    r2[2] = cdet2c(m[0], m[4], m[1], m[3]);
+}
+
+// ---------------------------------------------------------------- lattice
+
+// Site index s = x + Lx*(y + Ly*(z + Lz*t)).  An xy-plane is the Lx*Ly block of
+// one (z, t); plane index p = z + Lz*t.
+struct Lat {
+    int L[4];
+    int stride[4];  // 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int V;
+    int P;         // Lx*Ly
+    int nplanes;   // Lz*Lt
+};
+
+__device__ __forceinline__ int site_shift(const Lat& d, int s, int c_mu, int mu, int dir)
+{
+    // c_mu is the mu coordinate of s; dir = +1 or -1 with periodic wrap
+    if (dir > 0) return (c_mu == d.L[mu] - 1) ? s - (d.L[mu] - 1) * d.stride[mu] : s + d.stride[mu];
+    return (c_mu == 0) ? s + (d.L[mu] - 1) * d.stride[mu] : s - d.stride[mu];
+}
+
+__device__ __forceinline__ void site_coords(const Lat& d, int s, int c[4])
+{
+    c[0] = s % d.L[0];
+    int r = s / d.L[0];
+    c[1] = r % d.L[1];
+    r /= d.L[1];
+    c[2] = r % d.L[2];
+    c[3] = r / d.L[2];
+}
+
+// ---------------------------------------------------------------- control
+
+// Device-resident loop state of one gauge fixing.  The Delta kernel's last
+// block writes theta and F and decides whether the running loop stops.
+struct Ctl {
+    double theta;          // of the current links
+    double F;
+    double tol;            // stop threshold of the running phase
+    double tol_final;      // threshold of the FP64 phase
+    double alpha;          // steepest-descent step
+    int iter;              // updates applied (all phases)
+    int max_iter;
+    int phase;             // 0: FP32 phase of the mixed mode, 1: FP64
+    int phase_done;        // the running loop has met its stop condition
+    int done;              // the whole fix is over
+    int converged;
+    int nan_seen;
+    int iter_phase0;       // updates applied in the FP32 phase
+    unsigned int ticket;   // last-block counter of the reduction
+    unsigned int body_runs;
+    int hist_cap;
+    int pad;
+};
+
+}  // namespace lgf

@@ -1,0 +1,53 @@
+// FP64 instantiation of the iteration kernels, plus the conversion, input-check
+// and precision-switch kernels (all FP64).
+#include "lgf_launch_impl.cuh"
+
+namespace lgf {
+
+LGF_INSTANTIATE(double)
+
+namespace {
+inline unsigned blocks(long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
+}  // namespace
+
+void launch_pack_links64(cudaStream_t s, int V, const double* in, double2* U, unsigned long long* err)
+{
+    k_pack_links<double><<<blocks(4L * V, 256), 256, 0, s>>>(V, in, U, err, 1);
+}
+void launch_unpack_su3_64(cudaStream_t s, int V, int nmat, const double2* U, double* out)
+{
+    k_unpack_su3<double><<<blocks((long)nmat * V, 256), 256, 0, s>>>(V, nmat, U, out);
+}
+void launch_identity_rows64(cudaStream_t s, int V, double2* G)
+{
+    k_identity_rows<double><<<blocks(V, 256), 256, 0, s>>>(V, G);
+}
+void launch_pack_delta(cudaStream_t s, int V, const double* in, double2* Fd)
+{
+    k_pack_delta<<<blocks(V, 256), 256, 0, s>>>(V, in, Fd);
+}
+void launch_unpack_delta(cudaStream_t s, int V, const double2* Fd, double* out)
+{
+    k_unpack_delta<<<blocks(V, 256), 256, 0, s>>>(V, Fd, out);
+}
+void launch_unpack_full(cudaStream_t s, int V, const double2* g, double* out)
+{
+    k_unpack_full<<<blocks(V, 256), 256, 0, s>>>(V, g, out);
+}
+void launch_mixed_prep(cudaStream_t s, int V, const double2* U64, float2* U32, float2* G32, const Ctl* ctl)
+{
+    k_mixed_prep<<<blocks(V, 256), 256, 0, s>>>(V, U64, U32, G32, ctl);
+}
+void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
+                   Ctl* ctl)
+{
+    k_switch_gs<<<blocks(d.V, 256), 256, 0, s>>>(d.V, G32, Gs, ctl);
+    k_project<<<blocks(d.V, 256), 256, 0, s>>>(d, U64, G64, Gs, ctl);
+    k_phase_switch<<<1, 1, 0, s>>>(ctl);
+}
+void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h)
+{
+    k_loop_ctl<<<1, 1, 0, s>>>(ctl, h, 0x7fffffffu);
+}
+
+}  // namespace lgf

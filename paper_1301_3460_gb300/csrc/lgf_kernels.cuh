@@ -1,0 +1,380 @@
+// Kernels of one Fourier-accelerated steepest-descent iteration (arXiv:1301.3460):
+//
+//   k_delta      Delta(x) = (M - M^dag) - Tr(M - M^dag)/3, M = sum_mu [U_mu(x-mu) - U_mu(x)],
+//                packed into four complex fields, theta and F reduced in FP64, then
+//                the forward FFT along x and y of the xy-plane.
+//   k_zt         forward FFT along z and t, the accelerator p2max/(p2(k) V)
+//                (zero mode removed), inverse FFT along t and z.
+//   k_xyinv_g    inverse FFT along x and y, then g(x) = reunit(1 + alpha/2 Delta~(x))
+//                by row Gram-Schmidt in FP64.
+//   k_update     U_mu(x) <- g(x) U_mu(x) g^dag(x+mu) and G(x) <- g(x) G(x).
+//
+// Storage (structure of arrays, one plane of V complex numbers per entry):
+//   links U  [mu=4][e=6][V]  rows 0,1 of U_mu(x), e = 3 i + j; row 2 is rebuilt
+//                            as conj(row0 x row1) on every load (12-real form)
+//   G        [6][V]          rows 0,1 of the accumulated gauge transformation
+//   g        [9][V]          the full 3x3 g(x), read by up to nine sites
+//   fields   [4][V]          Delta01, Delta02, Delta12 and i*(Im Delta00) + ... packed
+//                            as (Im Delta00) + i (Im Delta11)
+// Delta is anti-Hermitian and traceless, so these four complex numbers carry
+// its eight real degrees of freedom; the accelerator is real and even in k, so
+// it maps each packed real pair to a real pair and the packing commutes with it.
+#pragma once
+#include "lgf_common.cuh"
+#include "lgf_fft.cuh"
+
+namespace lgf {
+
+__device__ __forceinline__ int ld_flag(const int* p) { return *(const volatile int*)p; }
+
+// ---------------------------------------------------------------- reductions
+
+constexpr int kMaxThreads = 512;  // block size bound of every plane-tiled kernel
+
+__device__ __forceinline__ double block_sum(double v, double* scratch /* kMaxThreads/32 */)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) scratch[w] = v;
+    __syncthreads();
+    double r = 0;
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int i = 0; i < nw; i++) r += scratch[i];
+    }
+    return r;  // valid in thread 0
+}
+
+// Per-block partial sums of theta and F, then the last block to finish sums
+// the partials in block order (deterministic) and updates the loop state.
+static __device__ void reduce_theta_F(double th, double f, double* __restrict__ partials, Ctl* ctl, double2* hist, int V)
+{
+    __shared__ double scratch[kMaxThreads / 32];
+    __shared__ int am_last;
+    double bt = block_sum(th, scratch);
+    double bf = block_sum(f, scratch);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = bt;
+        partials[2 * blockIdx.x + 1] = bf;
+        __threadfence();
+        unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+        am_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double a = 0, b = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        a += __ldcg(partials + 2 * i);
+        b += __ldcg(partials + 2 * i + 1);
+    }
+    a = block_sum(a, scratch);
+    b = block_sum(b, scratch);
+    if (threadIdx.x == 0) {
+        const double theta = a / (3.0 * (double)V);
+        const double F = b / (12.0 * (double)V);
+        ctl->theta = theta;
+        ctl->F = F;
+        const int it = ctl->iter;
+        if (hist != nullptr && ctl->hist_cap > 0) hist[it % ctl->hist_cap] = make_double2(theta, F);
+        if (!(theta == theta) || !(F == F) || isinf(theta)) {
+            ctl->nan_seen = 1;
+            ctl->phase_done = 1;
+            ctl->done = 1;
+        } else if (theta < ctl->tol) {
+            ctl->phase_done = 1;
+            if (ctl->phase == 1) {
+                ctl->done = 1;
+                ctl->converged = 1;
+            }
+        } else if (it >= ctl->max_iter) {
+            ctl->phase_done = 1;
+            ctl->done = 1;
+        }
+        ctl->ticket = 0u;
+        __threadfence();
+    }
+}
+
+// ---------------------------------------------------------------- link loads
+
+// rows 0,1 of link (mu, s) and the rebuilt row 2
+template <typename T>
+__device__ __forceinline__ void load_link(const vec2_t<T>* __restrict__ U, int V, int mu, int s, cx<T>* u)
+{
+#pragma unroll
+    for (int e = 0; e < 6; e++) u[e] = ld<T>(U + (size_t)(mu * 6 + e) * V + s);
+    complete_row2(u, u + 6);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_g(const vec2_t<T>* __restrict__ g, int V, int s, cx<T>* m)
+{
+#pragma unroll
+    for (int e = 0; e < 9; e++) m[e] = ld<T>(g + (size_t)e * V + s);
+}
+
+// ---------------------------------------------------------------- k_delta
+
+// One block per xy-plane.  Shared memory: (4 + nfc) * P complex values.  FFT = false
+// stores the packed Delta itself (used to check the stencil on its own).
+template <typename T, bool FFT>
+__global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, const vec2_t<T>* __restrict__ U,
+                                                       vec2_t<T>* __restrict__ Fd, double* __restrict__ partials,
+                                                       Ctl* ctl, double2* hist, const vec2_t<T>* __restrict__ twx,
+                                                       const vec2_t<T>* __restrict__ twy)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    if (ld_flag(&ctl->phase_done)) return;
+    const int P = d.P, V = d.V;
+    const int plane = blockIdx.x;
+    const int s0 = plane * P;
+    const int z = plane % d.L[2], t = plane / d.L[2];
+    double th = 0.0, fsum = 0.0;
+    for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
+        const int s = s0 + xy;
+        const int x = xy % d.L[0], y = xy / d.L[0];
+        const int c[4] = {x, y, z, t};
+        cx<T> M[9];
+#pragma unroll
+        for (int e = 0; e < 9; e++) M[e] = mk<T>(0, 0);
+        T tr = 0;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            cx<T> u[9];
+            load_link<T>(U, V, mu, s, u);
+            tr += u[0].re + u[4].re + u[8].re;
+#pragma unroll
+            for (int e = 0; e < 9; e++) M[e] = M[e] - u[e];
+            const int sb = site_shift(d, s, c[mu], mu, -1);
+            load_link<T>(U, V, mu, sb, u);
+#pragma unroll
+            for (int e = 0; e < 9; e++) M[e] = M[e] + u[e];
+        }
+        fsum += (double)tr;
+        // Delta_ij = M_ij - conj(M_ji); diagonal: 2 i Im M_ii minus a third of the trace
+        cx<T> d01 = M[1] - conjg(M[3]);
+        cx<T> d02 = M[2] - conjg(M[6]);
+        cx<T> d12 = M[5] - conjg(M[7]);
+        const T third = (T)(1.0 / 3.0);
+        const T trI = (M[0].im + M[4].im + M[8].im) * third;
+        const T a = (T)2 * (M[0].im - trI);
+        const T b = (T)2 * (M[4].im - trI);
+        const T cc = a + b;
+        th += 2.0 * ((double)norm2(d01) + (double)norm2(d02) + (double)norm2(d12)) + (double)a * a +
+              (double)b * b + (double)cc * cc;
+        vec2_t<T> v;
+        v.x = d01.re; v.y = d01.im; sm[xy] = v;
+        v.x = d02.re; v.y = d02.im; sm[P + xy] = v;
+        v.x = d12.re; v.y = d12.im; sm[2 * P + xy] = v;
+        v.x = a; v.y = b; sm[3 * P + xy] = v;
+    }
+    reduce_theta_F(th, fsum, partials, ctl, hist, V);
+    __syncthreads();
+    // forward FFT along x (lines: fields x Ly rows) and along y (fields x Lx columns)
+    if (FFT) fft_xy_fields<T>(F, P, sm, sm + 4 * P, twx, twy, kFwd);
+    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+        const int f = i / P, xy = i - f * P;
+        Fd[(size_t)f * V + s0 + xy] = sm[i];
+    }
+}
+
+// ---------------------------------------------------------------- k_zt
+
+// One block per (x-chunk of xw columns, y, field).  Shared memory: two buffers of
+// xw * Lz * Lt values laid out [t][z][xi].  Data arrive transformed along x and
+// y, so the x and y indices are the momenta kx, ky.
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t<T>* __restrict__ Fd, const Ctl* ctl,
+                                                    const vec2_t<T>* __restrict__ twz,
+                                                    const vec2_t<T>* __restrict__ twt, const double* __restrict__ s2x,
+                                                    const double* __restrict__ s2y, const double* __restrict__ s2z,
+                                                    const double* __restrict__ s2t, double p2max)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    if (ld_flag(&ctl->phase_done)) return;
+    const int XW = Z.xw;
+    const int Lz = d.L[2], Lt = d.L[3], P = d.P;
+    const int x0 = blockIdx.x * XW, y = blockIdx.y, f = blockIdx.z;
+    vec2_t<T>* base = Fd + (size_t)f * d.V + x0 + d.L[0] * y;
+    const int n = XW * Lz * Lt;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int zt = i / XW, xi = i - zt * XW;
+        sm[i] = base[xi + (size_t)P * zt];
+    }
+    __syncthreads();
+    vec2_t<T>* a = sm;
+    vec2_t<T>* b = sm + n;
+    // forward along z and t
+    vec2_t<T>* r = fft_lines<T>(Z.pz, a, b, Z.lz, 1, Z.mz, twz, kFwd);
+    r = fft_lines<T>(Z.pt, r, r == a ? b : a, Z.lt, 1, Z.mt, twt, kFwd);
+    // the accelerator p2max / (p2(k) V), zero mode removed
+    const double inv_v = 1.0 / (double)d.V;
+    const double sy = s2y[y];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int zt = i / XW, xi = i - zt * XW;
+        const int kt = zt / Lz, kz = zt - kt * Lz;
+        const double p2 = s2x[x0 + xi] + sy + s2z[kz] + s2t[kt];
+        const T mult = (p2 > 0.0) ? (T)(p2max / p2 * inv_v) : (T)0;
+        vec2_t<T> v = r[i];
+        v.x *= mult;
+        v.y *= mult;
+        r[i] = v;
+    }
+    __syncthreads();
+    // inverse along t and z
+    r = fft_lines<T>(Z.pt, r, r == a ? b : a, Z.lt, 1, Z.mt, twt, kInv);
+    r = fft_lines<T>(Z.pz, r, r == a ? b : a, Z.lz, 1, Z.mz, twz, kInv);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int zt = i / XW, xi = i - zt * XW;
+        base[xi + (size_t)P * zt] = r[i];
+    }
+}
+
+// ---------------------------------------------------------------- k_xyinv_g
+
+// row Gram-Schmidt of rows 0,1 of X in FP64; g gets all three rows
+__device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>* g /* 9 out */)
+{
+    double n0 = norm2(X[0]) + norm2(X[1]) + norm2(X[2]);
+    n0 = rsqrt(n0);
+    g[0] = X[0] * n0;
+    g[1] = X[1] * n0;
+    g[2] = X[2] * n0;
+    // <r0, X1> = sum conj(r0_j) X1_j
+    cx<double> ip = cmulc(X[3], g[0]);
+    ip = cmacc(ip, X[4], g[1]);
+    ip = cmacc(ip, X[5], g[2]);
+    cx<double> r1[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) r1[j] = X[3 + j] - cmul(ip, g[j]);
+    double n1 = rsqrt(norm2(r1[0]) + norm2(r1[1]) + norm2(r1[2]));
+    g[3] = r1[0] * n1;
+    g[4] = r1[1] * n1;
+    g[5] = r1[2] * n1;
+    complete_row2(g, g + 6);
+}
+
+// One block per xy-plane.  g is built in FP64 whatever T is, and stored as TG.
+template <typename T, typename TG>
+__global__ void __launch_bounds__(kMaxThreads) k_xyinv_g(Lat d, const XyFft F, const vec2_t<T>* __restrict__ Fd,
+                                                         vec2_t<TG>* __restrict__ g,
+                                                const Ctl* ctl, const vec2_t<T>* __restrict__ twx,
+                                                const vec2_t<T>* __restrict__ twy)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    if (ld_flag(&ctl->phase_done)) return;
+    const int P = d.P, V = d.V;
+    const int s0 = blockIdx.x * P;
+    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+        const int f = i / P, xy = i - f * P;
+        sm[i] = Fd[(size_t)f * V + s0 + xy];
+    }
+    __syncthreads();
+    fft_xy_fields<T>(F, P, sm, sm + 4 * P, twx, twy, kInv);
+    const double h = 0.5 * ctl->alpha;
+    for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
+        vec2_t<T> f0 = sm[xy], f1 = sm[P + xy], f2 = sm[2 * P + xy], f3 = sm[3 * P + xy];
+        // X = 1 + (alpha/2) Delta~ ; rows 0 and 1
+        cx<double> X[6];
+        X[0] = mk<double>(1.0, h * (double)f3.x);
+        X[1] = mk<double>(h * (double)f0.x, h * (double)f0.y);
+        X[2] = mk<double>(h * (double)f1.x, h * (double)f1.y);
+        X[3] = mk<double>(-h * (double)f0.x, h * (double)f0.y);  // -conj(Delta01)
+        X[4] = mk<double>(1.0, h * (double)f3.y);
+        X[5] = mk<double>(h * (double)f2.x, h * (double)f2.y);
+        cx<double> gm[9];
+        reunit_rows(X, gm);
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+            vec2_t<TG> v;
+            v.x = (TG)gm[e].re;
+            v.y = (TG)gm[e].im;
+            g[(size_t)e * V + s0 + xy] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- k_update
+
+// One thread per site.  G may be null (gauge not tracked).
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(Lat d, vec2_t<T>* __restrict__ U, vec2_t<T>* __restrict__ G,
+                                               const vec2_t<T>* __restrict__ g, Ctl* ctl)
+{
+    if (ld_flag(&ctl->phase_done)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->iter += 1;
+        if (ctl->phase == 0) ctl->iter_phase0 += 1;
+    }
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    int c[4];
+    site_coords(d, s, c);
+    cx<T> gx[9];
+    load_g<T>(g, V, s, gx);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        cx<T> u[9];
+        load_link<T>(U, V, mu, s, u);
+        // A = rows 0,1 of g(x) U
+        cx<T> A[6];
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<T> acc = cmul(gx[3 * i], u[j]);
+                acc = cmac(acc, gx[3 * i + 1], u[3 + j]);
+                acc = cmac(acc, gx[3 * i + 2], u[6 + j]);
+                A[3 * i + j] = acc;
+            }
+        cx<T> gn[9];
+        load_g<T>(g, V, site_shift(d, s, c[mu], mu, +1), gn);
+        // U' = A g^dag(x+mu): U'_ij = sum_k A_ik conj(gn_jk)
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<T> acc = cmulc(A[3 * i], gn[3 * j]);
+                acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
+                acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
+                st<T>(U + (size_t)(mu * 6 + 3 * i + j) * V + s, acc);
+            }
+    }
+    if (G != nullptr) {
+        cx<T> Gm[9];
+#pragma unroll
+        for (int e = 0; e < 6; e++) Gm[e] = ldv<T>(G + (size_t)e * V + s);
+        complete_row2(Gm, Gm + 6);
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<T> acc = cmul(gx[3 * i], Gm[j]);
+                acc = cmac(acc, gx[3 * i + 1], Gm[3 + j]);
+                acc = cmac(acc, gx[3 * i + 2], Gm[6 + j]);
+                st<T>(G + (size_t)(3 * i + j) * V + s, acc);
+            }
+    }
+}
+
+// ---------------------------------------------------------------- loop control
+
+// Last node of the while-loop body: keep looping while the running phase has
+// not met its stop condition; a hard bound on body runs makes the loop finite
+// whatever the state says.
+static __global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h, unsigned int bound)
+{
+    unsigned int n = ctl->body_runs + 1u;
+    ctl->body_runs = n;
+    const int cont = !ld_flag(&ctl->phase_done) && n < bound && n < (unsigned int)ctl->max_iter + 2u;
+    cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+}  // namespace lgf

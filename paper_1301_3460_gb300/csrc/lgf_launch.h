@@ -1,0 +1,55 @@
+// Host-side launch interface between the C ABI (lgf_capi.cu) and the kernel
+// translation units (lgf_k64.cu: FP64 kernels and the conversion kernels,
+// lgf_k32.cu: FP32 kernels).  Splitting by precision keeps each unit small and
+// lets them compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lgf_common.cuh"
+#include "lgf_fft.cuh"
+
+namespace lgf {
+
+// per-axis twiddle tables exp(-2 pi i m / L_mu), momentum table 4 sin^2(pi k / L_mu)
+struct Tables {
+    const double2* tw64[4];
+    const float2* tw32[4];
+    const double* s2[4];
+    double p2max;
+};
+
+// launch shape and FFT plans of the plane-tiled kernels of one precision
+struct Shape {
+    int nt_xy;   // threads of the xy-plane kernels
+    int nt_zt;   // threads of the zt-pencil kernel
+    XyFft xy;    // x and y transforms, chunks of nfc fields
+    ZtFft zt;    // z and t transforms of pencils of xw columns
+};
+
+template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh);
+template <typename T>
+void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* U,
+                  vec2_t<T>* Fd, double* partials, Ctl* ctl, double2* hist, bool fft);
+template <typename T>
+void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl);
+template <typename T>
+void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* Fd,
+                    vec2_t<T>* g, const Ctl* ctl);
+template <typename T>
+void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, bool inv);
+template <typename T>
+void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, const vec2_t<T>* g, Ctl* ctl);
+
+// conversion, checking and mode-switch kernels (FP64 unit)
+void launch_pack_links64(cudaStream_t s, int V, const double* in, double2* U, unsigned long long* err);
+void launch_unpack_su3_64(cudaStream_t s, int V, int nmat, const double2* U, double* out);
+void launch_identity_rows64(cudaStream_t s, int V, double2* G);
+void launch_pack_delta(cudaStream_t s, int V, const double* in, double2* Fd);
+void launch_unpack_delta(cudaStream_t s, int V, const double2* Fd, double* out);
+void launch_unpack_full(cudaStream_t s, int V, const double2* g, double* out);
+void launch_mixed_prep(cudaStream_t s, int V, const double2* U64, float2* U32, float2* G32, const Ctl* ctl);
+void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
+                   Ctl* ctl);
+void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h);
+
+}  // namespace lgf

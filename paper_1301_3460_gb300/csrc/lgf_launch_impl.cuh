@@ -1,0 +1,89 @@
+// Definitions of the templated launchers of lgf_launch.h; included by the
+// per-precision translation units, which instantiate them.
+#pragma once
+#include "lgf_aux.cuh"
+#include "lgf_launch.h"
+
+namespace lgf {
+
+template <typename T> inline const vec2_t<T>* tw_of(const Tables& tb, int mu);
+template <> inline const double2* tw_of<double>(const Tables& tb, int mu) { return tb.tw64[mu]; }
+template <> inline const float2* tw_of<float>(const Tables& tb, int mu) { return tb.tw32[mu]; }
+
+template <typename T> inline size_t xy_smem(const Lat& d, const Shape& sh)
+{
+    return (size_t)(4 + sh.xy.nfc) * d.P * sizeof(vec2_t<T>);
+}
+template <typename T> inline size_t zt_smem(const Lat& d, const Shape& sh)
+{
+    return (size_t)2 * sh.zt.xw * d.L[2] * d.L[3] * sizeof(vec2_t<T>);
+}
+
+template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh)
+{
+    const int sx = (int)xy_smem<T>(d, sh), sz = (int)zt_smem<T>(d, sh);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_delta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_delta<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xyinv_g<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xy_fft<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xy_fft<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
+    return cudaFuncSetAttribute(k_zt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+}
+
+template <typename T>
+void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* U,
+                  vec2_t<T>* Fd, double* partials, Ctl* ctl, double2* hist, bool fft)
+{
+    const size_t sm = xy_smem<T>(d, sh);
+    if (fft)
+        k_delta<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, U, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
+                                                         tw_of<T>(tb, 1));
+    else
+        k_delta<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, U, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
+                                                          tw_of<T>(tb, 1));
+}
+
+template <typename T>
+void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl)
+{
+    dim3 grid(d.L[0] / sh.zt.xw, d.L[1], 4);
+    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.zt, Fd, ctl, tw_of<T>(tb, 2), tw_of<T>(tb, 3), tb.s2[0],
+                                                      tb.s2[1], tb.s2[2], tb.s2[3], tb.p2max);
+}
+
+template <typename T>
+void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* Fd,
+                    vec2_t<T>* g, const Ctl* ctl)
+{
+    k_xyinv_g<T, T><<<d.nplanes, sh.nt_xy, xy_smem<T>(d, sh), s>>>(d, sh.xy, Fd, g, ctl, tw_of<T>(tb, 0),
+                                                                   tw_of<T>(tb, 1));
+}
+
+template <typename T>
+void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, bool inv)
+{
+    const size_t sm = xy_smem<T>(d, sh);
+    if (inv)
+        k_xy_fft<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+    else
+        k_xy_fft<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+}
+
+template <typename T>
+void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, const vec2_t<T>* g, Ctl* ctl)
+{
+    k_update<T><<<(d.V + 255) / 256, 256, 0, s>>>(d, U, G, g, ctl);
+}
+
+#define LGF_INSTANTIATE(T)                                                                                        \
+    template cudaError_t prepare_kernels<T>(const Lat&, const Shape&);                                           \
+    template void launch_delta<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, const vec2_t<T>*,       \
+                                  vec2_t<T>*, double*, Ctl*, double2*, bool);                                     \
+    template void launch_zt<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, vec2_t<T>*, const Ctl*);    \
+    template void launch_xyinv_g<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, const vec2_t<T>*,     \
+                                    vec2_t<T>*, const Ctl*);                                                      \
+    template void launch_xy_fft<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, vec2_t<T>*, bool);      \
+    template void launch_update<T>(const Lat&, cudaStream_t, vec2_t<T>*, vec2_t<T>*, const vec2_t<T>*, Ctl*);
+
+}  // namespace lgf

@@ -21,6 +21,8 @@ Arrays are complex128 (4, V, 3, 3), site index s = x + Lx*(y + Ly*(z + Lz*t)).
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 _LAMBDA = np.zeros((8, 3, 3), np.complex128)
@@ -68,32 +70,62 @@ def haar_su3(rng: np.random.Generator, n: int) -> np.ndarray:
 
 
 def su3_exp_i(eps: float, A: np.ndarray) -> np.ndarray:
-    """exp(i eps A) for Hermitian A (..., 3, 3)."""
-    w, v = np.linalg.eigh(A)
-    return np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * eps * w), v.conj())
+    """exp(i eps A) for Hermitian A (..., 3, 3), from its eigen-decomposition
+    (torch's CPU eigh, which runs outside the GIL, when torch is importable)."""
+    try:
+        import torch
+
+        w, v = torch.linalg.eigh(torch.from_numpy(np.ascontiguousarray(A)))
+        w, v = w.numpy(), v.numpy()
+    except ImportError:  # pragma: no cover
+        w, v = np.linalg.eigh(A)
+    return (v * np.exp(1j * eps * w)[..., None, :]) @ np.conj(np.swapaxes(v, -1, -2))
 
 
 def _dagger(m):
     return np.conj(np.swapaxes(m, -1, -2))
 
 
-def rough_gauge_field(L, eps: float, seed: int, haar: bool = True, chunk: int = 1 << 18) -> np.ndarray:
-    """U_mu(x) = h(x) exp(i eps A_mu(x)) h^dag(x+mu); haar=False uses h = 1."""
+def _exp_chunk(args):
+    eps, w = args
+    return su3_exp_i(eps, np.einsum("sa,aij->sij", w, GENERATORS))
+
+
+def rough_gauge_field(L, eps: float, seed: int, haar: bool = True, chunk: int = 1 << 17,
+                      workers: int | None = None) -> np.ndarray:
+    """U_mu(x) = h(x) exp(i eps A_mu(x)) h^dag(x+mu); haar=False uses h = 1.
+
+    Large lattices spread the eigen-decompositions over a pool of threads
+    (numpy's linear algebra releases the GIL); all random draws happen before,
+    so the result does not depend on the pool."""
     L = [int(v) for v in L]
     V = volume(L)
     rng = np.random.default_rng(seed)
     h = haar_su3(rng, V) if haar else None
     w = rng.standard_normal((4, V, 8))
     U = np.empty((4, V, 3, 3), np.complex128)
-    for mu in range(4):
-        nb = neighbour(L, mu, +1)
-        for a in range(0, V, chunk):
-            b = min(V, a + chunk)
-            A = np.einsum("sa,aij->sij", w[mu, a:b], GENERATORS)
-            W = su3_exp_i(eps, A)
-            if haar:
-                W = h[a:b] @ W @ _dagger(h[nb[a:b]])
-            U[mu, a:b] = W
+    jobs = [(mu, a, min(V, a + chunk)) for mu in range(4) for a in range(0, V, chunk)]
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1) if 4 * V >= (1 << 20) else 1
+
+    def job(j):
+        mu, a, b = j
+        U[mu, a:b] = _exp_chunk((eps, w[mu, a:b]))
+
+    if workers > 1:
+        import concurrent.futures as cf
+
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(job, jobs))
+    else:
+        for j in jobs:
+            job(j)
+    if haar:
+        for mu in range(4):
+            nb = neighbour(L, mu, +1)
+            for a in range(0, V, chunk):
+                b = min(V, a + chunk)
+                U[mu, a:b] = h[a:b] @ U[mu, a:b] @ _dagger(h[nb[a:b]])
     return U
 
 

@@ -1,0 +1,248 @@
+"""Python binding of the CUDA gauge-fixing library (liblgf.so, C ABI in include/lgf.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  There is no CPU fallback; if the library or a CUDA device is missing
+the calls raise.
+
+Arrays follow the C ABI: links complex128 (4, V, 3, 3), gauge transformations
+and matrix fields complex128 (V, 3, 3), site s = x + Lx*(y + Ly*(z + Lz*t)).
+Each may be a numpy array (host) or a contiguous torch complex128 CUDA tensor
+(device; then the copy stays on the device).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LGF_OK = 0
+LGF_ERR_ARG = 1
+LGF_ERR_CUDA = 2
+LGF_ERR_NOT_SU3 = 3
+LGF_ERR_UNSUPPORTED_DIMS = 4
+LGF_ERR_NOT_CONVERGED = 5
+LGF_ERR_NAN = 6
+LGF_ERR_TIMEOUT = 7
+LGF_ERR_STATE = 8
+
+LGF_FP64 = 0
+LGF_MIXED = 1
+LGF_NO_GAUGE = 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LgfError(RuntimeError):
+    def __init__(self, status: int, call: str):
+        self.status = status
+        lib = _lib
+        msg = lib.lgf_strerror(status).decode() if lib else str(status)
+        detail = lib.lgf_last_error().decode() if (lib and status == LGF_ERR_CUDA) else ""
+        super().__init__("%s failed: %s (status %d)%s" % (call, msg, status, (": " + detail) if detail else ""))
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblgf.so (building it in-tree with nvcc if absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("liblgf.so is not built (%s); run paper_1301_3460_gb300/build.py" % path)
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        IP = ctypes.POINTER(ctypes.c_int)
+        DP = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "lgf_create": ([ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
+            "lgf_set_stream": ([P, P], I),
+            "lgf_set_links": ([P, P, I], I),
+            "lgf_fix": ([P, D, D, I, IP, DP, DP], I),
+            "lgf_get_links": ([P, P, I], I),
+            "lgf_get_gauge": ([P, P, I], I),
+            "lgf_get_history": ([P, DP, I, IP], I),
+            "lgf_get_stats": ([P, IP, IP], I),
+            "lgf_set_switch_tol": ([P, D], I),
+            "lgf_delta": ([P, P, I, DP, DP], I),
+            "lgf_accelerate": ([P, P, P, I], I),
+            "lgf_build_g": ([P, P, D, P, I], I),
+            "lgf_time_kernels": ([P, D, I, I, DP], I),
+            "lgf_destroy": ([P], None),
+            "lgf_strerror": ([I], ctypes.c_char_p),
+            "lgf_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int, call: str):
+    if status != LGF_OK:
+        raise LgfError(status, call)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _in_ptr(a, shape):
+    """(pointer, on_device, keepalive) of an input array."""
+    if _is_torch(a):
+        import torch
+
+        assert a.dtype == torch.complex128 and tuple(a.shape) == tuple(shape), (a.dtype, a.shape, shape)
+        if not a.is_cuda:
+            a = a.numpy()
+        else:
+            assert a.is_contiguous()
+            return ctypes.c_void_p(a.data_ptr()), 1, a
+    a = np.ascontiguousarray(a, dtype=np.complex128).reshape(shape)
+    return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+def _out(like, shape, device):
+    if device is not None:
+        import torch
+
+        t = torch.empty(shape, dtype=torch.complex128, device=device)
+        return t, ctypes.c_void_p(t.data_ptr()), 1
+    a = np.empty(shape, np.complex128)
+    return a, a.ctypes.data_as(ctypes.c_void_p), 0
+
+
+class Lattice:
+    """One gauge field on the GPU and its gauge-fixing state (an lgf_ctx)."""
+
+    def __init__(self, dims, mixed: bool = False, track_gauge: bool = True, stream=None):
+        lib = load()
+        self.dims = tuple(int(v) for v in dims)
+        self.V = int(np.prod(self.dims))
+        flags = (LGF_MIXED if mixed else LGF_FP64) | (0 if track_gauge else LGF_NO_GAUGE)
+        arr = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        _check(lib.lgf_create(arr, flags, ctypes.byref(h)), "lgf_create")
+        self._h = h
+        self._lib = lib
+        self.mixed = mixed
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lgf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(self._lib.lgf_set_stream(self._h, ctypes.c_void_p(raw or 0)), "lgf_set_stream")
+
+    def set_switch_tol(self, tol: float):
+        _check(self._lib.lgf_set_switch_tol(self._h, float(tol)), "lgf_set_switch_tol")
+
+    def set_links(self, U):
+        p, dev, keep = _in_ptr(U, (4, self.V, 3, 3))
+        _check(self._lib.lgf_set_links(self._h, p, dev), "lgf_set_links")
+        del keep
+
+    def fix(self, alpha: float = 0.08, tol: float = 1e-15, max_iter: int = 100000, check: bool = True) -> dict:
+        it = ctypes.c_int()
+        F = ctypes.c_double()
+        th = ctypes.c_double()
+        st = self._lib.lgf_fix(self._h, float(alpha), float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(F),
+                               ctypes.byref(th))
+        if check and st not in (LGF_OK, LGF_ERR_NOT_CONVERGED):
+            raise LgfError(st, "lgf_fix")
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._lib.lgf_get_stats(self._h, ctypes.byref(a), ctypes.byref(b))
+        return dict(status=st, iters=it.value, F=F.value, theta=th.value, converged=(st == LGF_OK),
+                    iters_fp32=a.value, iters_fp64=b.value)
+
+    def get_links(self, device=None):
+        out, p, dev = _out(None, (4, self.V, 3, 3), device)
+        _check(self._lib.lgf_get_links(self._h, p, dev), "lgf_get_links")
+        return out
+
+    def get_gauge(self, device=None):
+        out, p, dev = _out(None, (self.V, 3, 3), device)
+        _check(self._lib.lgf_get_gauge(self._h, p, dev), "lgf_get_gauge")
+        return out
+
+    def history(self, n_max: int = 1 << 16) -> np.ndarray:
+        buf = np.zeros(2 * n_max, np.float64)
+        w = ctypes.c_int()
+        _check(self._lib.lgf_get_history(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n_max,
+                                         ctypes.byref(w)), "lgf_get_history")
+        return buf[: 2 * w.value].reshape(-1, 2)
+
+    def delta(self, device=None):
+        out, p, dev = _out(None, (self.V, 3, 3), device)
+        th, F = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.lgf_delta(self._h, p, dev, ctypes.byref(th), ctypes.byref(F)), "lgf_delta")
+        return out, th.value, F.value
+
+    def accelerate(self, D):
+        p, dev_in, keep = _in_ptr(D, (self.V, 3, 3))
+        out, q, dev = _out(None, (self.V, 3, 3), keep.device if dev_in else None)
+        _check(self._lib.lgf_accelerate(self._h, p, q, dev), "lgf_accelerate")
+        del keep
+        return out
+
+    def build_g(self, Dt, alpha: float):
+        p, dev_in, keep = _in_ptr(Dt, (self.V, 3, 3))
+        out, q, dev = _out(None, (self.V, 3, 3), keep.device if dev_in else None)
+        _check(self._lib.lgf_build_g(self._h, p, float(alpha), q, dev), "lgf_build_g")
+        del keep
+        return out
+
+
+KERNELS = ("delta_xyfft", "zt_fft_accel", "xyifft_g", "update")
+
+
+def _time_kernels(self, alpha: float = 0.08, n_iter: int = 5, precision: int = 64) -> dict:
+    """Mean per-launch time (ms) of the four iteration kernels, launched one by one."""
+    ms = (ctypes.c_double * 4)()
+    _check(self._lib.lgf_time_kernels(self._h, float(alpha), int(n_iter), int(precision), ms), "lgf_time_kernels")
+    return dict(zip(KERNELS, list(ms)))
+
+
+Lattice.time_kernels = _time_kernels
+
+
+def fix(U, dims, alpha: float = 0.08, tol: float = 1e-15, max_iter: int = 100000, mixed: bool = False):
+    """One-shot convenience: gauge-fix U and return (links, G, info)."""
+    with Lattice(dims, mixed=mixed) as lat:
+        lat.set_links(U)
+        info = lat.fix(alpha, tol, max_iter)
+        return lat.get_links(), lat.get_gauge(), info

@@ -1,0 +1,48 @@
+"""Algorithmic bytes and floating-point operations of the iteration kernels.
+
+Per lattice site and per launch, counting each unique array element once
+(neighbour re-reads served by caches are not counted) and flops as real
+multiplies/adds (an FMA is 2), with the FFT at the conventional 5 N log2 N per
+complex transform of length N.
+
+FP64 path, per site (V sites per launch):
+  delta_xyfft   reads the links (4 x 12 reals, rows 0,1) and writes the four
+                packed Delta fields: 384 + 64 B.  Flops: rebuild row 2 of 8
+                links (8 x 42), M (8 x 9 complex adds = 144), Delta, theta, F
+                (46), x,y FFT of 4 fields (4 x 5 log2(Lx Ly)).
+  zt_fft_accel  reads and writes the 4 fields: 64 + 64 B.  Flops: forward and
+                inverse z,t FFT of 4 fields (2 x 4 x 5 log2(Lz Lt)) + scale (8).
+  xyifft_g      reads the 4 fields, writes g (full 3x3): 64 + 144 B.  Flops:
+                inverse x,y FFT (4 x 5 log2(Lx Ly)) + Gram-Schmidt and row 2 (134).
+  update        reads links, g, G; writes links and G: 384 + 144 + 96 + 384 + 96 B.
+                Flops: per link row-2 rebuild (42) and two 2x3 by 3x3 complex
+                products (2 x 132); G: rebuild (42) + one product (132).
+FP32 kernels move half the bytes of every array they keep in FP32 (links, G, g,
+fields); their flop counts are the same.
+"""
+from __future__ import annotations
+
+import math
+
+KERNELS = ("delta_xyfft", "zt_fft_accel", "xyifft_g", "update")
+
+
+def per_site(dims, precision: int = 64) -> dict:
+    Lx, Ly, Lz, Lt = (int(v) for v in dims)
+    w = 1.0 if precision == 64 else 0.5
+    lxy = math.log2(Lx * Ly)
+    lzt = math.log2(Lz * Lt)
+    return {
+        "delta_xyfft": dict(bytes=(384 + 64) * w, flops=8 * 42 + 144 + 46 + 4 * 5 * lxy),
+        "zt_fft_accel": dict(bytes=(64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
+        "xyifft_g": dict(bytes=(64 + 144) * w, flops=4 * 5 * lxy + 134),
+        "update": dict(bytes=(384 + 144 + 96 + 384 + 96) * w, flops=4 * (42 + 2 * 132) + 42 + 132),
+    }
+
+
+def per_iteration(dims, precision: int = 64) -> dict:
+    V = 1
+    for v in dims:
+        V *= int(v)
+    ps = per_site(dims, precision)
+    return dict(bytes=V * sum(k["bytes"] for k in ps.values()), flops=V * sum(k["flops"] for k in ps.values()))
