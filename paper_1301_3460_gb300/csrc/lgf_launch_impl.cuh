@@ -19,16 +19,31 @@ template <typename T> inline size_t zt_smem(const Lat& d, const Shape& sh)
     return (size_t)2 * sh.zt.xw * d.L[2] * d.L[3] * sizeof(vec2_t<T>);
 }
 
+template <typename K> inline cudaError_t allow_max_smem(K* kernel, int optin)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+// The dynamic shared-memory limit is a per-function attribute shared by every
+// context in the process, so it is raised to the device's opt-in maximum (a
+// permission, not a reservation) rather than to this lattice's need: a later
+// context with smaller planes must not lower it under an earlier one.
 template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh)
 {
-    const int sx = (int)xy_smem<T>(d, sh), sz = (int)zt_smem<T>(d, sh);
+    int dev = 0, optin = 0;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_delta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_delta<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_xyinv_g<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_xy_fft<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_xy_fft<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx))) return e;
-    return cudaFuncSetAttribute(k_zt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    if ((size_t)optin < xy_smem<T>(d, sh) + 1024 || (size_t)optin < zt_smem<T>(d, sh)) return cudaErrorInvalidValue;
+    if ((e = allow_max_smem(k_delta<T, true>, optin))) return e;
+    if ((e = allow_max_smem(k_delta<T, false>, optin))) return e;
+    if ((e = allow_max_smem(k_xyinv_g<T, T>, optin))) return e;
+    if ((e = allow_max_smem(k_xy_fft<T, false>, optin))) return e;
+    if ((e = allow_max_smem(k_xy_fft<T, true>, optin))) return e;
+    return allow_max_smem(k_zt<T>, optin);
 }
 
 template <typename T>

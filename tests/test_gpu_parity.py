@@ -177,3 +177,22 @@ def test_full_size_one_step():
         Ug = lat.get_links()
     assert np.max(np.abs(Ug - ref["U"])) < 1e-13
     assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+
+
+def test_contexts_of_different_sizes_coexist():
+    """Creating a context for a small lattice must not break a live one with larger planes."""
+    Lb, Ls = (16, 16, 16, 16), (4, 4, 4, 4)
+    U = field(Lb, seed=3)
+    big = lgf.Lattice(Lb)
+    small = lgf.Lattice(Ls)
+    try:
+        big.set_links(U)
+        r = big.fix(tol=0.0, max_iter=1)
+        ref = orc.fix(Lb, U, tol=0.0, max_iter=1)
+        assert r["iters"] == 1
+        assert np.max(np.abs(big.get_links() - ref["U"])) < 1e-13
+        small.set_links(field(Ls))
+        assert small.fix(tol=0.0, max_iter=1)["iters"] == 1
+    finally:
+        big.close()
+        small.close()
