@@ -141,6 +141,28 @@ int lgf_build_g(lgf_ctx* ctx, const double* Dt_in, double alpha, double* g_out, 
  */
 int lgf_time_kernels(lgf_ctx* ctx, double alpha, int n_iter, int precision, double* ms);
 
+/*
+ * lgf_accelerate_noalloc: lgf_accelerate without a context, for callers that
+ * cannot let a library allocate device memory (they have handed the GPU's
+ * memory to an allocator of their own, such as a framework's caching pool or a
+ * runtime's fixed arena).  The paper has no counterpart: this is an interface
+ * variant, not a step of the method.
+ *   dims      lattice extents as for lgf_create; additionally V <= 65536 sites
+ *             (e.g. 16^4) and planes that fit the shared-memory tiles, else
+ *             LGF_ERR_UNSUPPORTED_DIMS (use lgf_create + lgf_accelerate instead)
+ *   Delta_in  device pointer, [V][3][3] complex128, traceless anti-Hermitian
+ *   Dt_out    device pointer, [V][3][3] complex128, receives the result
+ *   cuda_stream  the cudaStream_t to run on (NULL = legacy default stream)
+ * The call allocates nothing: its scratch is a file-scope device array of about
+ * 4 MiB that every GPU loading the library holds until the process exits.  The
+ * first call on a device, with that device current, looks up the array's
+ * device address and sets kernel attributes; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (what must start at zero is cleared on every call); calls whose work
+ * overlaps on the GPU race on it.  Returns after the stream has finished.
+ */
+int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in, double* Dt_out, void* cuda_stream);
+
 /* Release all device memory of ctx.  NULL is a no-op. */
 void lgf_destroy(lgf_ctx* ctx);
 

@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
             "lgf_accelerate": ([P, P, P, I], I),
             "lgf_build_g": ([P, P, D, P, I], I),
             "lgf_time_kernels": ([P, D, I, I, DP], I),
+            "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
             "lgf_destroy": ([P], None),
             "lgf_strerror": ([I], ctypes.c_char_p),
             "lgf_last_error": ([], ctypes.c_char_p),
@@ -225,6 +226,20 @@ class Lattice:
         _check(self._lib.lgf_build_g(self._h, p, float(alpha), q, dev), "lgf_build_g")
         del keep
         return out
+
+
+def lgf_accelerate_noalloc(dims, Delta_in, Dt_out, stream=None) -> None:
+    """Context-free Fourier acceleration into a caller-provided output, with the
+    library's static device scratch (no device allocation by the call).
+    Delta_in and Dt_out: contiguous torch complex128 CUDA tensors (V, 3, 3)."""
+    lib = load()
+    V = int(np.prod([int(v) for v in dims]))
+    for t in (Delta_in, Dt_out):
+        assert _is_torch(t) and t.is_cuda and t.is_contiguous() and tuple(t.shape) == (V, 3, 3)
+    raw = getattr(stream, "cuda_stream", stream) or 0
+    arr = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(lib.lgf_accelerate_noalloc(arr, ctypes.c_void_p(Delta_in.data_ptr()), ctypes.c_void_p(Dt_out.data_ptr()),
+                                      ctypes.c_void_p(raw)), "lgf_accelerate_noalloc")
 
 
 KERNELS = ("delta_xyfft", "zt_fft_accel", "xyifft_g", "update")
