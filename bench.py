@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -246,6 +247,51 @@ def run_ours(args, dims):
         ttt.setdefault(str(EPS[k % len(EPS)]), dict(iters=r["iters"], ms=1000 * per_step[k], F=r["F"],
                                                      theta=r["theta"], converged=r["converged"]))
 
+    # the same workload in mixed precision (FP32 until theta < 1e-6, then FP64)
+    mixed = None
+    if not args.no_mixed:
+        latm = lgf.Lattice(dims, mixed=True, stream=stream)
+
+        def mstep(i):
+            latm.set_links(dev[i % len(dev)])
+            return latm.fix(args.alpha, args.tol, args.max_iter)
+
+        for k in range(args.warmup):
+            mstep(k)
+        torch.cuda.synchronize()
+        evm = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        minfo = []
+        evm[0].record(stream)
+        for k in range(args.steps):
+            minfo.append(mstep(k))
+            evm[k + 1].record(stream)
+        torch.cuda.synchronize()
+        mper = [evm[k].elapsed_time(evm[k + 1]) / 1000.0 for k in range(args.steps)]
+        Tm = sum(mper)
+        mit = sum(r["iters"] for r in minfo)
+        if pg:
+            t = torch.tensor([Tm], device="cuda", dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            n = torch.tensor([mit], device="cuda", dtype=torch.float64)
+            pg.all_reduce(n, op=pg.ReduceOp.SUM)
+            Tm, mit = float(t.item()), int(n.item())
+        launches += sum(5 + 5 * max(r["iters_fp32"], 1) + 5 * max(r["iters_fp64"], 1) for r in minfo)
+        mttt = {}
+        for k, r in enumerate(minfo):
+            e = str(EPS[k % len(EPS)])
+            f64 = ttt.get(e, {}).get("F")
+            mttt.setdefault(e, dict(iters_fp32=r["iters_fp32"], iters_fp64=r["iters_fp64"], ms=1000 * mper[k],
+                                    F=r["F"], theta=r["theta"], converged=r["converged"],
+                                    F_rel_diff_vs_fp64=(abs(r["F"] / f64 - 1) if f64 else None)))
+        mixed = {"value": mit / Tm, "unit": "iters/s", "ms_per_step": 1000 * Tm / args.steps,
+                 "speedup_time_to_theta_vs_fp64": T / Tm, "time_to_theta": mttt}
+        latm.set_links(dev[1])
+        msm = latm.time_kernels(args.alpha, n_iter=8, precision=32)
+        per32 = roofline.per_site(dims, 32)
+        mixed["kernels_fp32"] = {k: {"ms": msm[k], "gbs": per32[k]["bytes"] * V / msm[k] / 1e6,
+                                     "gflops": per32[k]["flops"] * V / msm[k] / 1e6} for k in msm}
+        latm.close()
+
     # end to end through the C ABI from pinned host memory, copies included
     e2e = None
     if not args.no_e2e:
@@ -309,7 +355,7 @@ def run_ours(args, dims):
             "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol,
                        "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
                        % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
-            "time_to_theta": ttt, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "time_to_theta": ttt, "mixed": mixed, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -187,10 +187,12 @@ static __global__ void k_mixed_prep(int V, const double2* __restrict__ U64, floa
     for (int e = 0; e < 6; e++) G32[(size_t)e * V + s] = make_float2((e == 0 || e == 4) ? 1.f : 0.f, 0.f);
 }
 
-// end of the FP32 phase: Gs = reunit(G32) in FP64, stored as full 3x3 planes
+// end of the FP32 phase: Gs = reunit(G32) in FP64, stored as full 3x3 planes.
+// Runs also when the FP32 phase used up max_iter, so that the stored links keep
+// its progress; only a NaN skips it.
 static __global__ void k_switch_gs(int V, const float2* __restrict__ G32, double2* __restrict__ Gs, const Ctl* ctl)
 {
-    if (ld_flag(&ctl->done)) return;
+    if (ld_flag(&ctl->nan_seen)) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
     cx<double> X[6], g[9];
@@ -208,7 +210,7 @@ static __global__ void k_switch_gs(int V, const float2* __restrict__ G32, double
 static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restrict__ U, double2* __restrict__ G,
                                                 const double2* __restrict__ Gs, const Ctl* ctl)
 {
-    if (ld_flag(&ctl->done)) return;
+    if (ld_flag(&ctl->nan_seen)) return;
     const int V = d.V;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;

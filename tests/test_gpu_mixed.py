@@ -1,0 +1,73 @@
+"""Mixed precision: FP32 Delta/FFT/update until theta < 1e-6, then an FP64
+finish from links rebuilt in FP64 as G U_in G^dag.  Checked against the FP64
+oracle (and the FP64 GPU path at full size): theta < 1e-15, F within 1e-12
+relative, links exactly on the gauge orbit of the input; the link difference
+to the FP64 result is reported."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1301_3460_gb300 import inputs
+from paper_1301_3460_gb300 import lgf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("L,seed", [((16, 16, 16, 16), 1601), ((24, 24, 24, 24), 2401), ((8, 8, 8, 8), 1001)])
+def test_mixed_matches_fp64_oracle(L, seed):
+    U = inputs.rough_gauge_field(L, 0.3, seed)
+    ref = orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=5000)
+    with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+        Um = lat.get_links()
+        G = lat.get_gauge()
+        hist = lat.history()
+    assert ref["converged"] and r["converged"] and r["theta"] < 1e-15
+    assert r["iters_fp32"] > 0 and r["iters_fp64"] > 0
+    assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+    # exactly on the input's gauge orbit (FP64 rounding only)
+    np.testing.assert_allclose(orc.gauge_transform(L, U, G), Um, atol=1e-13)
+    assert abs(orc.plaquette(L, Um) - orc.plaquette(L, U)) < 1e-13
+    uu = np.einsum("msij,mskj->msik", Um, Um.conj())
+    assert np.max(np.abs(uu - np.eye(3))) < 1e-13
+    err = float(np.max(np.abs(Um - ref["U"])))
+    print("mixed %s: iters %d (+%d fp64) vs oracle %d; max|U_mixed - U_fp64| = %.2e; dF/F = %.2e" % (
+        L, r["iters_fp32"], r["iters_fp64"], ref["iters"], err, abs(r["F"] / ref["F"] - 1)))
+    # the FP32 phase ends below the switch threshold
+    assert hist[r["iters_fp32"] - 1, 0] >= 1e-6
+
+
+def test_mixed_full_size_against_fp64_gpu():
+    """48^4 (radix-3 FFT lengths): the mixed result against the FP64 GPU path."""
+    L = (48, 48, 48, 48)
+    U = inputs.rough_gauge_field(L, 0.3, 4801)
+    with lgf.Lattice(L) as lat:
+        lat.set_links(U)
+        r64 = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+        U64 = lat.get_links()
+    with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_links(U)
+        rm = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+        Um = lat.get_links()
+    assert r64["converged"] and rm["converged"]
+    assert rm["F"] == pytest.approx(r64["F"], rel=1e-12)
+    err = float(np.max(np.abs(Um - U64)))
+    print("48^4: fp64 %d iters, mixed %d+%d iters, max|dU| = %.2e" % (r64["iters"], rm["iters_fp32"],
+                                                                     rm["iters_fp64"], err))
+    assert err < 1e-4
+
+
+def test_mixed_max_iter_in_fp32_phase_keeps_progress():
+    L = (8, 8, 8, 8)
+    U = inputs.rough_gauge_field(L, 0.3, 5)
+    with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=3)
+        Um = lat.get_links()
+        G = lat.get_gauge()
+    assert r["status"] == lgf.LGF_ERR_NOT_CONVERGED and r["iters"] == 3 and r["iters_fp64"] == 0
+    np.testing.assert_allclose(orc.gauge_transform(L, U, G), Um, atol=1e-13)
+    _, th0, F0 = orc.delta(L, U)
+    _, th3, F3 = orc.delta(L, Um)
+    assert F3 > F0
