@@ -127,10 +127,14 @@ class Clocks:
 
 # ---------------------------------------------------------------- traffic record
 
+KERNEL_SOURCES = ("lgf_common.cuh", "lgf_fft.cuh", "lgf_kernels.cuh")
+
+
 def csrc_hash():
+    """Hash of the sources that define the iteration kernels."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1301_3460_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in KERNEL_SOURCES:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
