@@ -142,6 +142,45 @@ int lgf_build_g(lgf_ctx* ctx, const double* Dt_in, double alpha, double* g_out, 
 int lgf_time_kernels(lgf_ctx* ctx, double alpha, int n_iter, int precision, double* ms);
 
 /*
+ * lgf_autotune: choose the launch shapes of the shared-memory FFT kernels (block
+ * sizes, fields per x,y transform, x-columns per z,t pencil) for this lattice by
+ * timing the candidates on the stored links; both precisions of a mixed
+ * context.  The choice is cached for the process by extents and precision.
+ * Needs lgf_set_links first (LGF_ERR_STATE otherwise).  Changes no result
+ * beyond rounding.
+ */
+int lgf_autotune(lgf_ctx* ctx);
+
+/*
+ * Batched ensembles (no counterpart in the paper's single-lattice runs): n
+ * lattices of possibly different extents, fixed together by one CUDA graph
+ * launch in which every lattice's device-resident loop is an independent branch,
+ * so lattices of uneven size and uneven convergence run concurrently and each
+ * retires when it meets its stop condition.
+ *
+ * lgf_batch_create: dims = [n][4] extents (each as for lgf_create), flags as for
+ *   lgf_create (LGF_MIXED recommended).  Allocates every lattice's state.
+ * lgf_batch_set_links: links of lattice i (layout and checks as lgf_set_links).
+ * lgf_batch_fix: the first call autotunes the FFT shapes of each distinct
+ *   extent; then one graph launch runs all lattices to theta < theta_tol or
+ *   max_iter.  Per-lattice outputs (arrays of n, each may be NULL): iters, F,
+ *   theta, status (an lgf_status), t_retire_ms = time from the start of the
+ *   launch to the lattice's retirement, measured on the GPU clock.  Returns
+ *   LGF_OK if every lattice converged, else the first non-OK status.
+ * lgf_batch_get_links / _get_gauge / _get_stats: as the single-lattice calls.
+ */
+typedef struct lgf_batch lgf_batch;
+int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out);
+int lgf_batch_set_stream(lgf_batch* b, void* cuda_stream);
+int lgf_batch_set_links(lgf_batch* b, int i, const double* U, int on_device);
+int lgf_batch_fix(lgf_batch* b, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta,
+                  int* status, double* t_retire_ms);
+int lgf_batch_get_links(lgf_batch* b, int i, double* U_out, int on_device);
+int lgf_batch_get_gauge(lgf_batch* b, int i, double* G_out, int on_device);
+int lgf_batch_get_stats(lgf_batch* b, int i, int* iters_fp32, int* iters_fp64);
+void lgf_batch_destroy(lgf_batch* b);
+
+/*
  * lgf_accelerate_noalloc: lgf_accelerate without a context, for callers that
  * cannot let a library allocate device memory (they have handed the GPU's
  * memory to an allocator of their own, such as a framework's caching pool or a

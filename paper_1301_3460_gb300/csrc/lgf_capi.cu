@@ -11,7 +11,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <array>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -91,19 +94,16 @@ namespace {
 
 // Shared-memory FFT tiles: an xy-plane of all four fields plus a scratch of
 // nfc fields, and two buffers of a pencil of xw x-columns over (z, t).
-bool pick_shape(const Lat& d, size_t elem, int prefer_nfc, int prefer_xw, Shape* sh)
+bool make_shape(const Lat& d, size_t elem, int nt_xy, int nfc, int nt_zt, int xw, Shape* sh)
 {
     const size_t budget = 220 * 1024;
     const int P = d.P;
-    int nfc = prefer_nfc;
-    while (nfc > 1 && (size_t)(4 + nfc) * P * elem > budget) nfc >>= 1;
+    if (nfc != 1 && nfc != 2 && nfc != 4) return false;
     if ((size_t)(4 + nfc) * P * elem > budget) return false;
     const int ZT = d.L[2] * d.L[3];
-    int xw = prefer_xw;
-    while (xw > 1 && (d.L[0] % xw || (size_t)2 * xw * ZT * elem > budget)) xw >>= 1;
-    if ((size_t)2 * xw * ZT * elem > budget) return false;
-    sh->nt_xy = 512;
-    sh->nt_zt = 512;
+    if (xw < 1 || d.L[0] % xw || (size_t)2 * xw * ZT * elem > budget) return false;
+    sh->nt_xy = nt_xy;
+    sh->nt_zt = nt_zt;
     XyFft& X = sh->xy;
     X.px = make_axis_plan(d.L[0]);
     X.py = make_axis_plan(d.L[1]);
@@ -121,6 +121,15 @@ bool pick_shape(const Lat& d, size_t elem, int prefer_nfc, int prefer_xw, Shape*
     Z.lt = make_lines((unsigned)(xw * d.L[2]));
     Z.xw = xw;
     return true;
+}
+
+// default shape: the largest scratch and pencil width up to the preferred ones that fit
+bool pick_shape(const Lat& d, size_t elem, int prefer_nfc, int prefer_xw, Shape* sh)
+{
+    for (int nfc = prefer_nfc; nfc >= 1; nfc >>= 1)
+        for (int xw = prefer_xw; xw >= 1; xw >>= 1)
+            if (make_shape(d, elem, 512, nfc, 512, xw, sh)) return true;
+    return false;
 }
 
 template <typename T> const Shape& shape_of(const lgf_ctx* c);
@@ -192,12 +201,10 @@ int add_loop(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, 
     return LGF_OK;
 }
 
-int build_graph(lgf_ctx* c)
+// Append the nodes of one lgf_fix of context c to graph after deps; deps
+// receives the terminal node.
+int append_fix(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps)
 {
-    if (c->exec) return LGF_OK;
-    cudaGraph_t graph;
-    CK(cudaGraphCreate(&graph, 0));
-    std::vector<cudaGraphNode_t> deps;
     double2* Fd64 = reinterpret_cast<double2*>(c->Fd);
     if (c->mixed) {
         CKR(capture_begin(c, graph, deps));
@@ -217,14 +224,39 @@ int build_graph(lgf_ctx* c)
         CKR(capture_end(c, deps));
         CKR(add_loop<double>(c, graph, deps, c->U64, c->track ? c->G64 : nullptr, c->g64));
     }
-    cudaError_t e = cudaGraphInstantiate(&c->exec, graph, 0);
+    return LGF_OK;
+}
+
+int instantiate(cudaGraph_t graph, cudaGraphExec_t* exec)
+{
+    cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         set_error("cudaGraphInstantiate", e, __FILE__, __LINE__);
-        c->exec = nullptr;
+        *exec = nullptr;
         return LGF_ERR_CUDA;
     }
     return LGF_OK;
+}
+
+int build_graph(lgf_ctx* c)
+{
+    if (c->exec) return LGF_OK;
+    cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    std::vector<cudaGraphNode_t> deps;
+    int r = append_fix(c, graph, deps);
+    if (r != LGF_OK) {
+        cudaGraphDestroy(graph);
+        return r;
+    }
+    return instantiate(graph, &c->exec);
+}
+
+void drop_graph(lgf_ctx* c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    c->exec = nullptr;
 }
 
 // ---------------------------------------------------------------- set-up
@@ -393,6 +425,196 @@ int reset_stage_ctl(lgf_ctx* c, double alpha = 0.0)
     return LGF_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+
+// Launch shapes of the plane-tiled kernels are chosen per lattice shape and
+// precision by timing the candidates on the context's own data; the choice is
+// kept for the process, so contexts of equal extents are tuned once.
+std::mutex g_tune_mutex;
+std::map<std::array<int, 5>, Shape> g_tuned;
+
+template <typename T> Shape& shape_ref(lgf_ctx* c);
+template <> Shape& shape_ref<double>(lgf_ctx* c) { return c->sh64; }
+template <> Shape& shape_ref<float>(lgf_ctx* c) { return c->sh32; }
+
+template <typename T> vec2_t<T>* links_of(lgf_ctx* c);
+template <> double2* links_of<double>(lgf_ctx* c) { return c->U64; }
+template <> float2* links_of<float>(lgf_ctx* c) { return c->U32; }
+template <typename T> vec2_t<T>* g_of(lgf_ctx* c);
+template <> double2* g_of<double>(lgf_ctx* c) { return c->g64; }
+template <> float2* g_of<float>(lgf_ctx* c) { return c->g32; }
+
+// mean time of `reps` launches of the xy kernels (which = 0) or the zt kernel (1)
+template <typename T> int time_shape(lgf_ctx* c, const Shape& sh, int which, float* ms)
+{
+    const int reps = 3;
+    cudaStream_t s = c->stream;
+    vec2_t<T>* Fd = reinterpret_cast<vec2_t<T>*>(c->Fd);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int r = 0; r <= reps; r++) {
+        if (r == 1) cudaEventRecord(e0, s);
+        if (which == 0) {
+            launch_delta<T>(c->lat, sh, c->tb, s, links_of<T>(c), Fd, c->partials, c->ctl_stage, nullptr, true);
+            launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g_of<T>(c), c->ctl_stage);
+        } else {
+            launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl_stage);
+        }
+    }
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        set_error("autotune timing", e, __FILE__, __LINE__);
+        return LGF_ERR_CUDA;
+    }
+    CK(cudaGetLastError());
+    *ms = t / reps;
+    return LGF_OK;
+}
+
+template <typename T> int autotune_prec(lgf_ctx* c)
+{
+    const size_t elem = sizeof(vec2_t<T>);
+    std::array<int, 5> key = {c->L[0], c->L[1], c->L[2], c->L[3], (int)elem};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            shape_ref<T>(c) = it->second;
+            return LGF_OK;
+        }
+    }
+    Shape best = shape_ref<T>(c);
+    float best_xy = 1e30f, best_zt = 1e30f;
+    const int nts[2] = {256, 512};
+    for (int nt : nts)
+        for (int nfc = 1; nfc <= 4; nfc <<= 1) {
+            Shape cand;
+            if (!make_shape(c->lat, elem, nt, nfc, best.nt_zt, best.zt.xw, &cand)) continue;
+            float ms;
+            CKR(time_shape<T>(c, cand, 0, &ms));
+            if (ms < best_xy) {
+                best_xy = ms;
+                best.nt_xy = cand.nt_xy;
+                best.xy = cand.xy;
+            }
+        }
+    for (int nt : nts)
+        for (int xw = 1; xw <= 16; xw <<= 1) {
+            Shape cand;
+            if (!make_shape(c->lat, elem, best.nt_xy, best.xy.nfc, nt, xw, &cand)) continue;
+            float ms;
+            CKR(time_shape<T>(c, cand, 1, &ms));
+            if (ms < best_zt) {
+                best_zt = ms;
+                best.nt_zt = cand.nt_zt;
+                best.zt = cand.zt;
+            }
+        }
+    shape_ref<T>(c) = best;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = best;
+    return LGF_OK;
+}
+
+int autotune_ctx(lgf_ctx* c)
+{
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(reset_stage_ctl(c, 0.08));
+    CKR(autotune_prec<double>(c));
+    if (c->mixed) {
+        launch_mixed_prep(c->stream, c->V, c->U64, c->U32, c->G32, c->ctl_stage);
+        CKR(autotune_prec<float>(c));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+    return LGF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- batch
+
+struct lgf_batch {
+    std::vector<lgf_ctx*> ctx;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long* stamps = nullptr;  // device: [0] start, [1 + i] retirement of configuration i
+    std::vector<unsigned long long> host_stamps;
+    double* stage = nullptr;
+    size_t stage_bytes = 0;
+    bool tuned = false;
+};
+
+namespace {
+
+void batch_free(lgf_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (lgf_ctx* c : b->ctx) {
+        if (c) {
+            free_all(c);
+            delete c;
+        }
+    }
+    if (b->stamps) cudaFree(b->stamps);
+    if (b->stage) cudaFree(b->stage);
+}
+
+int batch_build(lgf_batch* b)
+{
+    if (b->exec) return LGF_OK;
+    cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    std::vector<cudaGraphNode_t> root;
+    lgf_ctx* c0 = b->ctx[0];
+    int r = capture_begin(c0, graph, root);
+    if (r == LGF_OK) {
+        launch_stamp(c0->cap, b->stamps);
+        r = capture_end(c0, root);
+    }
+    for (size_t i = 0; i < b->ctx.size() && r == LGF_OK; i++) {
+        std::vector<cudaGraphNode_t> deps = root;  // every configuration is an independent branch
+        r = append_fix(b->ctx[i], graph, deps);
+        if (r == LGF_OK) r = capture_begin(b->ctx[i], graph, deps);
+        if (r == LGF_OK) {
+            launch_stamp(b->ctx[i]->cap, b->stamps + 1 + i);
+            r = capture_end(b->ctx[i], deps);
+        }
+    }
+    if (r != LGF_OK) {
+        cudaGraphDestroy(graph);
+        return r;
+    }
+    return instantiate(graph, &b->exec);
+}
+
+Ctl initial_ctl(const lgf_ctx* c, double alpha, double tol, int max_iter)
+{
+    Ctl h;
+    memset(&h, 0, sizeof h);
+    h.tol_final = tol;
+    h.tol = c->mixed ? (c->switch_tol > tol ? c->switch_tol : tol) : tol;
+    h.alpha = alpha;
+    h.max_iter = max_iter;
+    h.phase = c->mixed ? 0 : 1;
+    h.hist_cap = kHistCap;
+    return h;
+}
+
+int status_of(const Ctl& r)
+{
+    if (r.nan_seen) return LGF_ERR_NAN;
+    if (r.converged) return LGF_OK;
+    if (!r.done) return LGF_ERR_TIMEOUT;
+    return LGF_ERR_NOT_CONVERGED;
+}
+
 }  // namespace
 
 // ==================================================================== C ABI
@@ -484,15 +706,7 @@ int lgf_fix(lgf_ctx* c, double alpha, double theta_tol, int max_iter, int* iters
     if (!(alpha > 0) || !(theta_tol >= 0) || max_iter < 0) return LGF_ERR_ARG;
     if (!c->have_links) return LGF_ERR_STATE;
     CKR(build_graph(c));
-    Ctl h;
-    memset(&h, 0, sizeof h);
-    h.tol_final = theta_tol;
-    h.tol = c->mixed ? (c->switch_tol > theta_tol ? c->switch_tol : theta_tol) : theta_tol;
-    h.alpha = alpha;
-    h.max_iter = max_iter;
-    h.phase = c->mixed ? 0 : 1;
-    h.hist_cap = kHistCap;
-    *c->host_ctl = h;
+    *c->host_ctl = initial_ctl(c, alpha, theta_tol, max_iter);
     CK(cudaMemcpyAsync(c->ctl, c->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
     CK(cudaGraphLaunch(c->exec, c->stream));
     CK(cudaMemcpyAsync(c->host_ctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
@@ -505,10 +719,7 @@ int lgf_fix(lgf_ctx* c, double alpha, double theta_tol, int max_iter, int* iters
     if (iters) *iters = r.iter;
     if (F) *F = r.F;
     if (theta) *theta = r.theta;
-    if (r.nan_seen) return LGF_ERR_NAN;
-    if (r.converged) return LGF_OK;
-    if (!r.done) return LGF_ERR_TIMEOUT;
-    return LGF_ERR_NOT_CONVERGED;
+    return status_of(r);
 }
 
 int lgf_get_links(lgf_ctx* c, double* U_out, int on_device)
@@ -675,6 +886,141 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
     CK(cudaGetLastError());
     for (int k = 0; k < 4; k++) ms[k] = acc[k] / n_iter;
     return LGF_OK;
+}
+
+int lgf_autotune(lgf_ctx* c)
+{
+    if (!c) return LGF_ERR_ARG;
+    return autotune_ctx(c);
+}
+
+int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out)
+{
+    if (n < 1 || !dims || !out) return LGF_ERR_ARG;
+    *out = nullptr;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE)) return LGF_ERR_ARG;
+    lgf_batch* b = new (std::nothrow) lgf_batch();
+    if (!b) return LGF_ERR_ARG;
+    int r = LGF_OK;
+    for (int i = 0; i < n && r == LGF_OK; i++) {
+        lgf_ctx* c = new (std::nothrow) lgf_ctx();
+        if (!c) {
+            r = LGF_ERR_ARG;
+            break;
+        }
+        b->ctx.push_back(c);
+        r = create_impl(dims + 4 * i, flags, c);
+    }
+    if (r == LGF_OK) {
+        cudaError_t e = cudaMalloc((void**)&b->stamps, (n + 1) * sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            set_error("cudaMalloc", e, __FILE__, __LINE__);
+            r = LGF_ERR_CUDA;
+        }
+        b->host_stamps.assign(n + 1, 0ull);
+    }
+    if (r != LGF_OK) {
+        batch_free(b);
+        delete b;
+        return r;
+    }
+    *out = b;
+    return LGF_OK;
+}
+
+void lgf_batch_destroy(lgf_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
+}
+
+int lgf_batch_set_stream(lgf_batch* b, void* stream)
+{
+    if (!b) return LGF_ERR_ARG;
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    for (lgf_ctx* c : b->ctx) c->stream = b->stream;
+    return LGF_OK;
+}
+
+int lgf_batch_set_links(lgf_batch* b, int i, const double* U, int on_device)
+{
+    if (!b || !U || i < 0 || i >= (int)b->ctx.size()) return LGF_ERR_ARG;
+    lgf_ctx* c = b->ctx[i];
+    if (on_device) return lgf_set_links(c, U, 1);
+    // host arrays go through one staging buffer shared by the whole batch
+    const size_t bytes = (size_t)4 * c->V * 18 * sizeof(double);
+    if (b->stage_bytes < bytes) {
+        if (b->stage) cudaFree(b->stage);
+        b->stage = nullptr;
+        b->stage_bytes = 0;
+        CK(cudaMalloc((void**)&b->stage, bytes));
+        b->stage_bytes = bytes;
+    }
+    CK(cudaMemcpyAsync(b->stage, U, bytes, cudaMemcpyHostToDevice, c->stream));
+    return lgf_set_links(c, b->stage, 1);
+}
+
+int lgf_batch_fix(lgf_batch* b, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta,
+                  int* status, double* t_retire_ms)
+{
+    if (!b) return LGF_ERR_ARG;
+    if (!(alpha > 0) || !(theta_tol >= 0) || max_iter < 0) return LGF_ERR_ARG;
+    for (lgf_ctx* c : b->ctx)
+        if (!c->have_links) return LGF_ERR_STATE;
+    if (!b->tuned) {
+        // tune each distinct lattice shape once (the choice is cached for the process)
+        for (lgf_ctx* c : b->ctx) CKR(autotune_ctx(c));
+        b->tuned = true;
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    CKR(batch_build(b));
+    for (lgf_ctx* c : b->ctx) {
+        *c->host_ctl = initial_ctl(c, alpha, theta_tol, max_iter);
+        CK(cudaMemcpyAsync(c->ctl, c->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, b->stream));
+    }
+    CK(cudaGraphLaunch(b->exec, b->stream));
+    for (lgf_ctx* c : b->ctx) CK(cudaMemcpyAsync(c->host_ctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(b->host_stamps.data(), b->stamps, b->host_stamps.size() * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaGetLastError());
+    int worst = LGF_OK;
+    for (size_t i = 0; i < b->ctx.size(); i++) {
+        lgf_ctx* c = b->ctx[i];
+        const Ctl r = *c->host_ctl;
+        c->last_iters = r.iter;
+        c->last_iters32 = r.iter_phase0;
+        c->last_hist = r.iter + 1;
+        const int st = status_of(r);
+        if (iters) iters[i] = r.iter;
+        if (F) F[i] = r.F;
+        if (theta) theta[i] = r.theta;
+        if (status) status[i] = st;
+        if (t_retire_ms) t_retire_ms[i] = (double)(b->host_stamps[1 + i] - b->host_stamps[0]) * 1e-6;
+        if (st != LGF_OK && worst == LGF_OK) worst = st;
+    }
+    return worst;
+}
+
+int lgf_batch_get_links(lgf_batch* b, int i, double* U_out, int on_device)
+{
+    if (!b || i < 0 || i >= (int)b->ctx.size()) return LGF_ERR_ARG;
+    return lgf_get_links(b->ctx[i], U_out, on_device);
+}
+
+int lgf_batch_get_gauge(lgf_batch* b, int i, double* G_out, int on_device)
+{
+    if (!b || i < 0 || i >= (int)b->ctx.size()) return LGF_ERR_ARG;
+    return lgf_get_gauge(b->ctx[i], G_out, on_device);
+}
+
+int lgf_batch_get_stats(lgf_batch* b, int i, int* iters_fp32, int* iters_fp64)
+{
+    if (!b || i < 0 || i >= (int)b->ctx.size()) return LGF_ERR_ARG;
+    return lgf_get_stats(b->ctx[i], iters_fp32, iters_fp64);
 }
 
 }  // extern "C"

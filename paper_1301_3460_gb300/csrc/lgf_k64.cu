@@ -45,6 +45,14 @@ void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs,
     k_project<<<blocks(d.V, 256), 256, 0, s>>>(d, U64, G64, Gs, ctl);
     k_phase_switch<<<1, 1, 0, s>>>(ctl);
 }
+static __global__ void k_stamp(unsigned long long* p)
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    *p = t;
+}
+void launch_stamp(cudaStream_t s, unsigned long long* p) { k_stamp<<<1, 1, 0, s>>>(p); }
+
 void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h)
 {
     k_loop_ctl<<<1, 1, 0, s>>>(ctl, h, 0x7fffffffu);

@@ -51,5 +51,7 @@ void launch_mixed_prep(cudaStream_t s, int V, const double2* U64, float2* U32, f
 void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
                    Ctl* ctl);
 void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h);
+// writes the GPU's global nanosecond timer to *p
+void launch_stamp(cudaStream_t s, unsigned long long* p);
 
 }  // namespace lgf

@@ -150,3 +150,38 @@ def random_su3_algebra(rng: np.random.Generator, shape) -> np.ndarray:
     """X = sum_a w_a T_a, w_a ~ N(0,1): random Hermitian traceless matrices."""
     w = rng.standard_normal(tuple(shape) + (8,))
     return np.einsum("...a,aij->...ij", w, GENERATORS)
+
+
+def rough_gauge_field_torch(L, eps: float, seed: int, device="cuda", chunk: int = 1 << 20):
+    """The same distribution as rough_gauge_field, drawn on a torch device (for
+    large ensembles): h Haar-random SU(3) from the QR of complex Gaussians, A_mu
+    Gaussian in the Gell-Mann basis, exp(i eps A) by torch.linalg.matrix_exp.
+    Random stream: torch.Generator(device) seeded with seed; draws h, then w per
+    mu, chunk by chunk.  Returns a complex128 tensor (4, V, 3, 3) on device."""
+    import torch
+
+    L = [int(v) for v in L]
+    V = volume(L)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    T = torch.from_numpy(GENERATORS).to(device)
+    h = torch.empty((V, 3, 3), dtype=torch.complex128, device=device)
+    for a in range(0, V, chunk):
+        b = min(V, a + chunk)
+        z = torch.randn((b - a, 3, 3, 2), generator=g, dtype=torch.float64, device=device)
+        z = torch.complex(z[..., 0], z[..., 1]) / np.sqrt(2)
+        q, r = torch.linalg.qr(z)
+        d = torch.diagonal(r, dim1=-2, dim2=-1)
+        q = q * (d / d.abs()).unsqueeze(-2)
+        det = torch.linalg.det(q)
+        h[a:b] = q / (det ** (1.0 / 3.0)).reshape(-1, 1, 1)
+    U = torch.empty((4, V, 3, 3), dtype=torch.complex128, device=device)
+    for mu in range(4):
+        nb = torch.from_numpy(neighbour(L, mu, +1)).to(device)
+        for a in range(0, V, chunk):
+            b = min(V, a + chunk)
+            w = torch.randn((b - a, 8), generator=g, dtype=torch.float64, device=device).to(torch.complex128)
+            A = torch.einsum("sa,aij->sij", w, T)
+            W = torch.linalg.matrix_exp(1j * eps * A)
+            U[mu, a:b] = h[a:b] @ W @ h[nb[a:b]].conj().transpose(-1, -2)
+    return U

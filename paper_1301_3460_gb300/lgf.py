@@ -82,6 +82,15 @@ def load(build_if_missing: bool = True):
             "lgf_build_g": ([P, P, D, P, I], I),
             "lgf_time_kernels": ([P, D, I, I, DP], I),
             "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
+            "lgf_autotune": ([P], I),
+            "lgf_batch_create": ([I, ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
+            "lgf_batch_set_stream": ([P, P], I),
+            "lgf_batch_set_links": ([P, I, P, I], I),
+            "lgf_batch_fix": ([P, D, D, I, IP, DP, DP, IP, DP], I),
+            "lgf_batch_get_links": ([P, I, P, I], I),
+            "lgf_batch_get_gauge": ([P, I, P, I], I),
+            "lgf_batch_get_stats": ([P, I, IP, IP], I),
+            "lgf_batch_destroy": ([P], None),
             "lgf_destroy": ([P], None),
             "lgf_strerror": ([I], ctypes.c_char_p),
             "lgf_last_error": ([], ctypes.c_char_p),
@@ -253,6 +262,83 @@ def _time_kernels(self, alpha: float = 0.08, n_iter: int = 5, precision: int = 6
 
 
 Lattice.time_kernels = _time_kernels
+
+
+def _autotune(self) -> None:
+    """Pick the FFT kernels' launch shapes for this lattice by timing (needs links)."""
+    _check(self._lib.lgf_autotune(self._h), "lgf_autotune")
+
+
+Lattice.autotune = _autotune
+
+
+class Batch:
+    """An ensemble of lattices (possibly of different extents) fixed by one graph launch."""
+
+    def __init__(self, dims_list, mixed: bool = True, stream=None):
+        lib = load()
+        self.dims = [tuple(int(v) for v in d) for d in dims_list]
+        self.n = len(self.dims)
+        self.V = [int(np.prod(d)) for d in self.dims]
+        arr = (ctypes.c_int * (4 * self.n))(*[v for d in self.dims for v in d])
+        h = ctypes.c_void_p()
+        flags = LGF_MIXED if mixed else LGF_FP64
+        _check(lib.lgf_batch_create(self.n, arr, flags, ctypes.byref(h)), "lgf_batch_create")
+        self._h, self._lib = h, lib
+        if stream is not None:
+            raw = getattr(stream, "cuda_stream", stream)
+            _check(lib.lgf_batch_set_stream(h, ctypes.c_void_p(raw or 0)), "lgf_batch_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lgf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_links(self, i: int, U):
+        p, dev, keep = _in_ptr(U, (4, self.V[i], 3, 3))
+        _check(self._lib.lgf_batch_set_links(self._h, int(i), p, dev), "lgf_batch_set_links")
+        del keep
+
+    def fix(self, alpha: float = 0.08, tol: float = 1e-15, max_iter: int = 100000) -> dict:
+        n = self.n
+        it = (ctypes.c_int * n)()
+        F = (ctypes.c_double * n)()
+        th = (ctypes.c_double * n)()
+        st = (ctypes.c_int * n)()
+        tr = (ctypes.c_double * n)()
+        rc = self._lib.lgf_batch_fix(self._h, float(alpha), float(tol), int(max_iter), it, F, th, st, tr)
+        if rc not in (LGF_OK, LGF_ERR_NOT_CONVERGED):
+            raise LgfError(rc, "lgf_batch_fix")
+        a, b = ctypes.c_int(), ctypes.c_int()
+        i32, i64 = [], []
+        for i in range(n):
+            self._lib.lgf_batch_get_stats(self._h, i, ctypes.byref(a), ctypes.byref(b))
+            i32.append(a.value)
+            i64.append(b.value)
+        return dict(status=list(st), iters=list(it), F=list(F), theta=list(th), t_retire_ms=list(tr),
+                    iters_fp32=i32, iters_fp64=i64, rc=rc)
+
+    def get_links(self, i: int, device=None):
+        out, p, dev = _out(None, (4, self.V[i], 3, 3), device)
+        _check(self._lib.lgf_batch_get_links(self._h, int(i), p, dev), "lgf_batch_get_links")
+        return out
+
+    def get_gauge(self, i: int, device=None):
+        out, p, dev = _out(None, (self.V[i], 3, 3), device)
+        _check(self._lib.lgf_batch_get_gauge(self._h, int(i), p, dev), "lgf_batch_get_gauge")
+        return out
 
 
 def fix(U, dims, alpha: float = 0.08, tol: float = 1e-15, max_iter: int = 100000, mixed: bool = False):
