@@ -385,9 +385,17 @@ def run_ensemble(args):
     torch.cuda.set_device(local)
     dims = [d for n, d in ENSEMBLE for _ in range(n)]
     eps = np.random.default_rng(5000).uniform(0.15, 0.5, size=len(dims))
-    dev = [inputs.rough_gauge_field_torch(d, float(e), 5000 + i + 1000 * rank) for i, (d, e) in enumerate(zip(dims, eps))]
+    t0 = time.time()
+
+    def log(msg):
+        sys.stderr.write("[ensemble %.1fs] %s\n" % (time.time() - t0, msg))
+        sys.stderr.flush()
+
+    dev = [inputs.rough_gauge_field_cuda(d, float(e), 5000 + i + 1000 * rank) for i, (d, e) in enumerate(zip(dims, eps))]
+    log("generated %d lattices" % len(dev))
     stream = torch.cuda.current_stream()
     b = lgf.Batch(dims, mixed=True, stream=stream)
+    log("batch created")
 
     def step():
         for i, u in enumerate(dev):
@@ -395,7 +403,8 @@ def run_ensemble(args):
         return b.fix(args.alpha, args.tol, args.max_iter)
 
     for _ in range(max(1, args.warmup)):
-        step()
+        r = step()
+        log("warm-up step: iters %s" % r["iters"][:4])
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()

@@ -16,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblgf.so")
+INPUTS_SRC = os.path.join(HERE, "inputs_csrc", "lgf_inputs.cu")
+INPUTS_LIB = os.path.join(OUT_DIR, "liblgf_inputs.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -39,10 +41,13 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in _deps())
+    for lib, deps in ((LIB, _deps()), (INPUTS_LIB, [INPUTS_SRC, __file__])):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if any(os.path.getmtime(p) > t for p in deps):
+            return False
+    return True
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
@@ -65,8 +70,20 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj
 
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+
+    def build_inputs():
+        # the synthetic-input generator is a library of its own (no gauge-fixing code)
+        tmp = INPUTS_LIB + ".tmp%d" % os.getpid()
+        cmd = [cc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", INPUTS_SRC, "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (INPUTS_SRC, r.stdout, r.stderr))
+        os.replace(tmp, INPUTS_LIB)
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs) + 1, os.cpu_count() or 1))) as ex:
+        fut = ex.submit(build_inputs)
         objs = list(ex.map(compile_one, srcs))
+        fut.result()
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -152,36 +152,34 @@ def random_su3_algebra(rng: np.random.Generator, shape) -> np.ndarray:
     return np.einsum("...a,aij->...ij", w, GENERATORS)
 
 
-def rough_gauge_field_torch(L, eps: float, seed: int, device="cuda", chunk: int = 1 << 20):
-    """The same distribution as rough_gauge_field, drawn on a torch device (for
-    large ensembles): h Haar-random SU(3) from the QR of complex Gaussians, A_mu
-    Gaussian in the Gell-Mann basis, exp(i eps A) by torch.linalg.matrix_exp.
-    Random stream: torch.Generator(device) seeded with seed; draws h, then w per
-    mu, chunk by chunk.  Returns a complex128 tensor (4, V, 3, 3) on device."""
+def rough_gauge_field_cuda(L, eps: float, seed: int, haar: bool = True):
+    """The same distribution as rough_gauge_field, drawn on the current CUDA
+    device by the separate input-generation library (liblgf_inputs.so: Philox
+    counter-based random numbers, column Gram-Schmidt Haar matrices, Taylor
+    scaling-and-squaring exponential).  A different random stream from the numpy
+    generator.  Returns a complex128 torch tensor (4, V, 3, 3) on the device."""
+    import ctypes
+
     import torch
 
+    from . import build as _build
+
+    if not os.path.exists(_build.INPUTS_LIB) or not _build.up_to_date():
+        _build.build()
+    lib = ctypes.CDLL(_build.INPUTS_LIB)
+    f = lib.lgf_inputs_rough_field
+    f.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
     L = [int(v) for v in L]
     V = volume(L)
-    g = torch.Generator(device=device)
-    g.manual_seed(int(seed))
-    T = torch.from_numpy(GENERATORS).to(device)
-    h = torch.empty((V, 3, 3), dtype=torch.complex128, device=device)
-    for a in range(0, V, chunk):
-        b = min(V, a + chunk)
-        z = torch.randn((b - a, 3, 3, 2), generator=g, dtype=torch.float64, device=device)
-        z = torch.complex(z[..., 0], z[..., 1]) / np.sqrt(2)
-        q, r = torch.linalg.qr(z)
-        d = torch.diagonal(r, dim1=-2, dim2=-1)
-        q = q * (d / d.abs()).unsqueeze(-2)
-        det = torch.linalg.det(q)
-        h[a:b] = q / (det ** (1.0 / 3.0)).reshape(-1, 1, 1)
-    U = torch.empty((4, V, 3, 3), dtype=torch.complex128, device=device)
-    for mu in range(4):
-        nb = torch.from_numpy(neighbour(L, mu, +1)).to(device)
-        for a in range(0, V, chunk):
-            b = min(V, a + chunk)
-            w = torch.randn((b - a, 8), generator=g, dtype=torch.float64, device=device).to(torch.complex128)
-            A = torch.einsum("sa,aij->sij", w, T)
-            W = torch.linalg.matrix_exp(1j * eps * A)
-            U[mu, a:b] = h[a:b] @ W @ h[nb[a:b]].conj().transpose(-1, -2)
+    U = torch.empty((4, V, 3, 3), dtype=torch.complex128, device="cuda")
+    h = torch.empty((V, 3, 3), dtype=torch.complex128, device="cuda") if haar else None
+    rc = f((ctypes.c_int * 4)(*L), float(eps), int(seed), int(bool(haar)),
+           ctypes.c_void_p(h.data_ptr() if h is not None else 0), ctypes.c_void_p(U.data_ptr()),
+           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError("input generation failed (CUDA error %d)" % rc)
+    torch.cuda.current_stream().synchronize()
+    del h
     return U

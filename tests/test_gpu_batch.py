@@ -88,10 +88,10 @@ def test_autotune_keeps_results():
     assert np.max(np.abs(Um - ref["U"])) < 1e-4
 
 
-def test_torch_generator_is_su3():
-    torch = pytest.importorskip("torch")
+def test_cuda_generator_is_su3():
+    pytest.importorskip("torch")
     L = (8, 8, 4, 4)
-    U = inputs.rough_gauge_field_torch(L, 0.3, 3).cpu().numpy()
+    U = inputs.rough_gauge_field_cuda(L, 0.3, 3).cpu().numpy()
     uu = np.einsum("msij,mskj->msik", U, U.conj())
     assert np.max(np.abs(uu - np.eye(3))) < 1e-12
     assert np.max(np.abs(np.linalg.det(U) - 1)) < 1e-12
