@@ -181,6 +181,28 @@ int lgf_batch_get_stats(lgf_batch* b, int i, int* iters_fp32, int* iters_fp64);
 void lgf_batch_destroy(lgf_batch* b);
 
 /*
+ * Derivatives (no counterpart in the paper, which only fixes the gauge): the
+ * vector-Jacobian products of one Fourier-accelerated step and of the gluon
+ * propagator at the smallest momenta, FP64, for differentiating gauge-fixed
+ * observables with respect to the input links.  Gradients of a real loss L
+ * follow G = dL/dRe U + i dL/dIm U, i.e. dL = Re sum conj(G) dU.  Arrays are
+ * device pointers, complex128 [4][V][3][3] like the links.
+ *
+ * lgf_step_bwd: the stored links are the step's input U (rows 0,1 used, row 2
+ *   rebuilt); gU_out is the cotangent of the step's output U' (all three rows,
+ *   row 2 taken as its rebuild from rows 0,1); gU_in receives the cotangent of
+ *   U (row 2 zero: the step does not read it).  alpha as in lgf_fix.
+ * lgf_gluon_pmin: D = mean over the four momenta with one k_mu = 1 of
+ *   D(p) = 2/((N_c^2-1)(N_d-1)V) sum_mu Tr[A~_mu(p) A~_mu(p)^dag],
+ *   A_mu = (U - U^dag)/(2i) - trace/3, of the stored links; Dp[4] (may be NULL)
+ *   gets the four values.
+ * lgf_gluon_pmin_bwd: gU = gD * dD/dU of the stored links (row 2 zero).
+ */
+int lgf_step_bwd(lgf_ctx* ctx, double alpha, const double* gU_out, double* gU_in);
+int lgf_gluon_pmin(lgf_ctx* ctx, double* D, double* Dp);
+int lgf_gluon_pmin_bwd(lgf_ctx* ctx, double gD, double* gU);
+
+/*
  * lgf_accelerate_noalloc: lgf_accelerate without a context, for callers that
  * cannot let a library allocate device memory (they have handed the GPU's
  * memory to an allocator of their own, such as a framework's caching pool or a

@@ -88,6 +88,16 @@ struct lgf_ctx {
     double switch_tol = 1e-6;
     cudaGraphExec_t exec = nullptr;
     int last_iters = 0, last_iters32 = 0, last_hist = 0;
+    // workspace of the derivative entry points (allocated on first use)
+    double2* dGp = nullptr;   // [4][9][V] cotangent in / out
+    double2* dGud = nullptr;  // [4][9][V]
+    double2* dQ = nullptr;    // [4][9][V]
+    double2* dGgs = nullptr;  // [6][V]
+    double2* dFA = nullptr;   // [4][V]
+    double2* dFB = nullptr;   // [4][V]
+    double2* gl_part = nullptr;
+    double2* gl_At = nullptr;  // [16][9]
+    double* gl_D = nullptr;    // [5]
 };
 
 namespace {
@@ -372,7 +382,8 @@ void free_all(lgf_ctx* c)
 {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
-                    c->hist, c->err, c->stage, c->tables};
+                    c->hist, c->err, c->stage, c->tables, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
+                    c->gl_part, c->gl_At, c->gl_D};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_ctl) cudaFreeHost(c->host_ctl);
@@ -533,6 +544,28 @@ int autotune_ctx(lgf_ctx* c)
     }
     CK(cudaStreamSynchronize(c->stream));
     drop_graph(c);
+    return LGF_OK;
+}
+
+int ensure_diff(lgf_ctx* c)
+{
+    if (c->dGp) return LGF_OK;
+    const size_t Vs = (size_t)c->V;
+    CKR(alloc((void**)&c->dGp, 36 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->dGud, 36 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->dQ, 36 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->dGgs, 6 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->dFA, 4 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->dFB, 4 * Vs * sizeof(double2)));
+    return LGF_OK;
+}
+
+int ensure_gluon(lgf_ctx* c)
+{
+    if (c->gl_part) return LGF_OK;
+    CKR(alloc((void**)&c->gl_part, (size_t)16 * gluon_blocks(c->V) * 9 * sizeof(double2)));
+    CKR(alloc((void**)&c->gl_At, 144 * sizeof(double2)));
+    CKR(alloc((void**)&c->gl_D, 5 * sizeof(double)));
     return LGF_OK;
 }
 
@@ -1021,6 +1054,66 @@ int lgf_batch_get_stats(lgf_batch* b, int i, int* iters_fp32, int* iters_fp64)
 {
     if (!b || i < 0 || i >= (int)b->ctx.size()) return LGF_ERR_ARG;
     return lgf_get_stats(b->ctx[i], iters_fp32, iters_fp64);
+}
+
+int lgf_step_bwd(lgf_ctx* c, double alpha, const double* gU_out, double* gU_in)
+{
+    if (!c || !gU_out || !gU_in || !(alpha > 0)) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(ensure_diff(c));
+    CKR(reset_stage_ctl(c, alpha));
+    cudaStream_t s = c->stream;
+    double2* Fd = reinterpret_cast<double2*>(c->Fd);
+    // forward of the step on the stored links, up to g and the spatial Delta~
+    launch_delta<double>(c->lat, c->sh64, c->tb, s, c->U64, Fd, c->partials, c->ctl_stage, nullptr, true);
+    launch_zt<double>(c->lat, c->sh64, c->tb, s, Fd, c->ctl_stage);
+    launch_xy_fft<double>(c->lat, c->sh64, c->tb, s, Fd, true);
+    launch_g_from_dt(s, c->V, Fd, c->g64, alpha);
+    // backward
+    launch_pack_full(s, c->V, gU_out, c->dGp);
+    launch_step_bwd(s, c->lat, c->U64, c->g64, Fd, c->dGp, c->dGud, c->dGgs, c->dQ, alpha, c->dFA, c->dFB);
+    for (double2* F : {c->dFA, c->dFB}) {
+        launch_xy_fft<double>(c->lat, c->sh64, c->tb, s, F, false);
+        launch_zt<double>(c->lat, c->sh64, c->tb, s, F, c->ctl_stage);
+        launch_xy_fft<double>(c->lat, c->sh64, c->tb, s, F, true);
+    }
+    launch_bwd_delta(s, c->lat, c->U64, c->dFA, c->dFB, c->dGud, c->dGp);
+    launch_unpack_planes(s, c->V, c->dGp, gU_in);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return LGF_OK;
+}
+
+int lgf_gluon_pmin(lgf_ctx* c, double* D, double* Dp)
+{
+    if (!c || !D) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(ensure_gluon(c));
+    launch_gluon(c->stream, c->lat, c->U64, c->tb, c->gl_part, c->gl_At, c->gl_D);
+    double h[5];
+    CK(cudaMemcpyAsync(h, c->gl_D, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    *D = h[4];
+    if (Dp)
+        for (int i = 0; i < 4; i++) Dp[i] = h[i];
+    return LGF_OK;
+}
+
+int lgf_gluon_pmin_bwd(lgf_ctx* c, double gD, double* gU)
+{
+    if (!c || !gU) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(ensure_gluon(c));
+    CKR(ensure_diff(c));
+    // the forward's Fourier sums, then dD/dU
+    launch_gluon(c->stream, c->lat, c->U64, c->tb, c->gl_part, c->gl_At, c->gl_D);
+    const double coef = gD * 2.0 / (8.0 * 3.0 * (double)c->V) / 4.0 * 2.0;
+    launch_gluon_bwd(c->stream, c->lat, c->U64, c->gl_At, coef, c->tb, c->dGp);
+    launch_unpack_planes(c->stream, c->V, c->dGp, gU);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return LGF_OK;
 }
 
 }  // extern "C"

@@ -1,5 +1,6 @@
 // FP64 instantiation of the iteration kernels, plus the conversion, input-check
 // and precision-switch kernels (all FP64).
+#include "lgf_diff.cuh"
 #include "lgf_launch_impl.cuh"
 
 namespace lgf {
@@ -52,6 +53,44 @@ static __global__ void k_stamp(unsigned long long* p)
     *p = t;
 }
 void launch_stamp(cudaStream_t s, unsigned long long* p) { k_stamp<<<1, 1, 0, s>>>(p); }
+
+void launch_g_from_dt(cudaStream_t s, int V, const double2* Fd, double2* g, double alpha)
+{
+    k_g_from_dt<<<blocks(V, 256), 256, 0, s>>>(V, Fd, g, alpha);
+}
+void launch_pack_full(cudaStream_t s, int V, const double* in, double2* out)
+{
+    k_pack_full<<<blocks(4L * V, 256), 256, 0, s>>>(V, in, out);
+}
+void launch_unpack_planes(cudaStream_t s, int V, const double2* in, double* out)
+{
+    k_unpack_planes<<<blocks(4L * V, 256), 256, 0, s>>>(V, in, out);
+}
+void launch_step_bwd(cudaStream_t s, const Lat& d, const double2* U, const double2* g, const double2* Fdt,
+                     double2* Gp, double2* Gud, double2* Ggs, double2* Q, double alpha, double2* FA, double2* FB)
+{
+    k_bwd_update<<<blocks(d.V, 128), 128, 0, s>>>(d, U, g, Gp, Gud, Ggs, Q);
+    k_bwd_reunit<<<blocks(d.V, 256), 256, 0, s>>>(d, Fdt, Ggs, Q, alpha, FA, FB);
+}
+void launch_bwd_delta(cudaStream_t s, const Lat& d, const double2* U, const double2* FA, const double2* FB,
+                      const double2* Gud, double2* Gin)
+{
+    k_bwd_delta<<<blocks(d.V, 256), 256, 0, s>>>(d, U, FA, FB, Gud, Gin);
+}
+int gluon_blocks(int V) { int nb = (V + 255) / 256; return nb < 608 ? nb : 608; }
+void launch_gluon(cudaStream_t s, const Lat& d, const double2* U, const Tables& tb, double2* part, double2* At,
+                  double* D)
+{
+    const int nbx = gluon_blocks(d.V);
+    k_gluon_partial<<<dim3(nbx, 16), 256, 0, s>>>(d, U, tb.tw64[0], tb.tw64[1], tb.tw64[2], tb.tw64[3], part);
+    const double c = 2.0 / (8.0 * 3.0 * (double)d.V);
+    k_gluon_final<<<1, 160, 0, s>>>(nbx, c, part, At, D);
+}
+void launch_gluon_bwd(cudaStream_t s, const Lat& d, const double2* U, const double2* At, double coef, const Tables& tb,
+                      double2* Gout)
+{
+    k_gluon_bwd<<<blocks(d.V, 256), 256, 0, s>>>(d, U, At, coef, tb.tw64[0], tb.tw64[1], tb.tw64[2], tb.tw64[3], Gout);
+}
 
 void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h)
 {

@@ -51,6 +51,19 @@ void launch_mixed_prep(cudaStream_t s, int V, const double2* U64, float2* U32, f
 void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
                    Ctl* ctl);
 void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h);
+// derivative of one step and of the gluon propagator (lgf_diff.cuh)
+void launch_g_from_dt(cudaStream_t s, int V, const double2* Fd, double2* g, double alpha);
+void launch_pack_full(cudaStream_t s, int V, const double* in, double2* out);
+void launch_unpack_planes(cudaStream_t s, int V, const double2* in, double* out);
+void launch_step_bwd(cudaStream_t s, const Lat& d, const double2* U, const double2* g, const double2* Fdt,
+                     double2* Gp, double2* Gud, double2* Ggs, double2* Q, double alpha, double2* FA, double2* FB);
+void launch_bwd_delta(cudaStream_t s, const Lat& d, const double2* U, const double2* FA, const double2* FB,
+                      const double2* Gud, double2* Gin);
+int gluon_blocks(int V);
+void launch_gluon(cudaStream_t s, const Lat& d, const double2* U, const Tables& tb, double2* part, double2* At,
+                  double* D);
+void launch_gluon_bwd(cudaStream_t s, const Lat& d, const double2* U, const double2* At, double coef, const Tables& tb,
+                      double2* Gout);
 // writes the GPU's global nanosecond timer to *p
 void launch_stamp(cudaStream_t s, unsigned long long* p);
 

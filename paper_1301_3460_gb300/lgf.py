@@ -83,6 +83,9 @@ def load(build_if_missing: bool = True):
             "lgf_time_kernels": ([P, D, I, I, DP], I),
             "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
             "lgf_autotune": ([P], I),
+            "lgf_step_bwd": ([P, D, P, P], I),
+            "lgf_gluon_pmin": ([P, DP, DP], I),
+            "lgf_gluon_pmin_bwd": ([P, D, P], I),
             "lgf_batch_create": ([I, ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
             "lgf_batch_set_stream": ([P, P], I),
             "lgf_batch_set_links": ([P, I, P, I], I),
@@ -270,6 +273,40 @@ def _autotune(self) -> None:
 
 
 Lattice.autotune = _autotune
+
+
+def _step_bwd(self, g_out, alpha: float = 0.08):
+    """Cotangent of the stored links (the step's input) from the cotangent g_out of
+    the step's output; both contiguous complex128 CUDA tensors (4, V, 3, 3)."""
+    import torch
+
+    assert _is_torch(g_out) and g_out.is_cuda and g_out.dtype == torch.complex128
+    g_out = g_out.contiguous()
+    g_in = torch.empty_like(g_out)
+    _check(self._lib.lgf_step_bwd(self._h, float(alpha), ctypes.c_void_p(g_out.data_ptr()),
+                                  ctypes.c_void_p(g_in.data_ptr())), "lgf_step_bwd")
+    return g_in
+
+
+def _gluon_pmin(self):
+    """(mean, [D(p) for the four momenta with one k_mu = 1]) of the stored links."""
+    D = ctypes.c_double()
+    Dp = (ctypes.c_double * 4)()
+    _check(self._lib.lgf_gluon_pmin(self._h, ctypes.byref(D), Dp), "lgf_gluon_pmin")
+    return D.value, list(Dp)
+
+
+def _gluon_pmin_bwd(self, gD: float = 1.0, device="cuda"):
+    import torch
+
+    g = torch.empty((4, self.V, 3, 3), dtype=torch.complex128, device=device)
+    _check(self._lib.lgf_gluon_pmin_bwd(self._h, float(gD), ctypes.c_void_p(g.data_ptr())), "lgf_gluon_pmin_bwd")
+    return g
+
+
+Lattice.step_bwd = _step_bwd
+Lattice.gluon_pmin = _gluon_pmin
+Lattice.gluon_pmin_bwd = _gluon_pmin_bwd
 
 
 class Batch:
