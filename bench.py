@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble")
     return ap.parse_args()
@@ -298,6 +299,27 @@ def run_ours(args, dims):
                                      "gflops": per32[k]["flops"] * V / msm[k] / 1e6} for k in msm}
         latm.close()
 
+    # differentiation: forward + backward of a K-step unroll with checkpoints and D(p_min)
+    diff = None
+    if not args.no_diff:
+        from paper_1301_3460_gb300 import autograd as lad
+
+        Kd, every = 10, 5
+        lat_d = lgf.Lattice(dims, track_gauge=False, stream=stream)
+        for rep in range(2):  # the first pass warms up
+            U0 = dev[1].clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            D, _ = lad.gluon_after_fixing(U0, dims, K=Kd, every=every, lat=lat_d)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            D.backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+        lat_d.close()
+        diff = {"steps": Kd, "checkpoint_every": every, "fwd_ms": 1000 * (t1 - t0), "bwd_ms": 1000 * (t2 - t1),
+                "fwd_bwd_steps_per_s": Kd / (t2 - t0), "D_pmin": float(D.item())}
+
     # end to end through the C ABI from pinned host memory, copies included
     e2e = None
     if not args.no_e2e:
@@ -361,7 +383,7 @@ def run_ours(args, dims):
             "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol,
                        "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
                        % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
-            "time_to_theta": ttt, "mixed": mixed, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "time_to_theta": ttt, "mixed": mixed, "diff": diff, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

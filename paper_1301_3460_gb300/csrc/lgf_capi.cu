@@ -83,6 +83,7 @@ struct lgf_ctx {
     double* stage = nullptr;  // device staging for host arrays
     size_t stage_bytes = 0;
     void* tables = nullptr;
+    void* mult = nullptr;     // multiplier tables: V doubles then V floats
     Ctl* host_ctl = nullptr;  // pinned
     bool have_links = false;
     double switch_tol = 1e-6;
@@ -321,6 +322,16 @@ int build_tables(lgf_ctx* c)
         off += L;
     }
     CK(cudaMemcpy(c->tables, h.data(), bytes, cudaMemcpyHostToDevice));
+    // p2max/(p2(k) V) for every momentum, in both precisions
+    const size_t Vs = (size_t)c->V;
+    CKR(alloc(&c->mult, Vs * (sizeof(double) + sizeof(float))));
+    double* m64 = reinterpret_cast<double*>(c->mult);
+    float* m32 = reinterpret_cast<float*>(m64 + Vs);
+    launch_make_mult(nullptr, c->lat, c->tb, m64, m32);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    c->tb.mult64 = m64;
+    c->tb.mult32 = m32;
     return LGF_OK;
 }
 
@@ -382,7 +393,7 @@ void free_all(lgf_ctx* c)
 {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
-                    c->hist, c->err, c->stage, c->tables, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
+                    c->hist, c->err, c->stage, c->tables, c->mult, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
                     c->gl_part, c->gl_At, c->gl_D};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -54,6 +54,10 @@ static __global__ void k_stamp(unsigned long long* p)
 }
 void launch_stamp(cudaStream_t s, unsigned long long* p) { k_stamp<<<1, 1, 0, s>>>(p); }
 
+void launch_make_mult(cudaStream_t s, const Lat& d, const Tables& tb, double* m64, float* m32)
+{
+    k_make_mult<<<blocks(d.V, 256), 256, 0, s>>>(d, tb.s2[0], tb.s2[1], tb.s2[2], tb.s2[3], tb.p2max, m64, m32);
+}
 void launch_g_from_dt(cudaStream_t s, int V, const double2* Fd, double2* g, double alpha)
 {
     k_g_from_dt<<<blocks(V, 256), 256, 0, s>>>(V, Fd, g, alpha);

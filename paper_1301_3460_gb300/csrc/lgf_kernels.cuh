@@ -164,8 +164,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, con
         const T a = (T)2 * (M[0].im - trI);
         const T b = (T)2 * (M[4].im - trI);
         const T cc = a + b;
-        th += 2.0 * ((double)norm2(d01) + (double)norm2(d02) + (double)norm2(d12)) + (double)a * a +
-              (double)b * b + (double)cc * cc;
+        // per-site sum of |Delta_ij|^2 in the kernel's precision, accumulated over
+        // sites in FP64
+        th += (double)((T)2 * (norm2(d01) + norm2(d02) + norm2(d12)) + a * a + b * b + cc * cc);
         vec2_t<T> v;
         v.x = d01.re; v.y = d01.im; sm[xy] = v;
         v.x = d02.re; v.y = d02.im; sm[P + xy] = v;
@@ -190,9 +191,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, con
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t<T>* __restrict__ Fd, const Ctl* ctl,
                                                     const vec2_t<T>* __restrict__ twz,
-                                                    const vec2_t<T>* __restrict__ twt, const double* __restrict__ s2x,
-                                                    const double* __restrict__ s2y, const double* __restrict__ s2z,
-                                                    const double* __restrict__ s2t, double p2max)
+                                                    const vec2_t<T>* __restrict__ twt, const T* __restrict__ mult,
+                                                    const double* __restrict__ s2x, const double* __restrict__ s2y,
+                                                    const double* __restrict__ s2z, const double* __restrict__ s2t,
+                                                    double p2max)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
@@ -212,18 +214,31 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
     // forward along z and t
     vec2_t<T>* r = fft_lines<T>(Z.pz, a, b, Z.lz, 1, Z.mz, twz, kFwd);
     r = fft_lines<T>(Z.pt, r, r == a ? b : a, Z.lt, 1, Z.mt, twt, kFwd);
-    // the accelerator p2max / (p2(k) V), zero mode removed
-    const double inv_v = 1.0 / (double)d.V;
-    const double sy = s2y[y];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int zt = i / XW, xi = i - zt * XW;
-        const int kt = zt / Lz, kz = zt - kt * Lz;
-        const double p2 = s2x[x0 + xi] + sy + s2z[kz] + s2t[kt];
-        const T mult = (p2 > 0.0) ? (T)(p2max / p2 * inv_v) : (T)0;
-        vec2_t<T> v = r[i];
-        v.x *= mult;
-        v.y *= mult;
-        r[i] = v;
+    // the accelerator p2max / (p2(k) V), zero mode removed: from the table of
+    // multipliers (site-indexed by momentum) when there is one, else computed
+    if (mult != nullptr) {
+        const T* mrow = mult + x0 + d.L[0] * y;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int zt = i / XW, xi = i - zt * XW;
+            const T m = __ldg(mrow + xi + (size_t)P * zt);
+            vec2_t<T> v = r[i];
+            v.x *= m;
+            v.y *= m;
+            r[i] = v;
+        }
+    } else {
+        const double inv_v = 1.0 / (double)d.V;
+        const double sy = s2y[y];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int zt = i / XW, xi = i - zt * XW;
+            const int kt = zt / Lz, kz = zt - kt * Lz;
+            const double p2 = s2x[x0 + xi] + sy + s2z[kz] + s2t[kt];
+            const T m = (p2 > 0.0) ? (T)(p2max / p2 * inv_v) : (T)0;
+            vec2_t<T> v = r[i];
+            v.x *= m;
+            v.y *= m;
+            r[i] = v;
+        }
     }
     __syncthreads();
     // inverse along t and z
@@ -235,10 +250,25 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
     }
 }
 
+// multiplier table p2max / (p2(k) V) for every momentum k (site-indexed), FP64 and FP32
+static __global__ void k_make_mult(Lat d, const double* __restrict__ s2x, const double* __restrict__ s2y,
+                                   const double* __restrict__ s2z, const double* __restrict__ s2t, double p2max,
+                                   double* __restrict__ m64, float* __restrict__ m32)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.V) return;
+    int c[4];
+    site_coords(d, s, c);
+    const double p2 = s2x[c[0]] + s2y[c[1]] + s2z[c[2]] + s2t[c[3]];
+    const double m = (p2 > 0.0) ? p2max / p2 / (double)d.V : 0.0;
+    m64[s] = m;
+    m32[s] = (float)m;
+}
+
 // ---------------------------------------------------------------- k_xyinv_g
 
-// row Gram-Schmidt of rows 0,1 of X in FP64; g gets all three rows
-__device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>* g /* 9 out */)
+// row Gram-Schmidt of rows 0,1 of X in FP64: the orthonormal rows 0,1 of g
+__device__ __forceinline__ void gram_schmidt01(const cx<double>* X /* 6 in */, cx<double>* g /* 6 out */)
 {
     double n0 = norm2(X[0]) + norm2(X[1]) + norm2(X[2]);
     n0 = rsqrt(n0);
@@ -256,6 +286,12 @@ __device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>
     g[3] = r1[0] * n1;
     g[4] = r1[1] * n1;
     g[5] = r1[2] * n1;
+}
+
+// all three rows in FP64: row 2 = conj(r0 x r1)
+__device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>* g /* 9 out */)
+{
+    gram_schmidt01(X, g);
     complete_row2(g, g + 6);
 }
 
@@ -288,15 +324,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_xyinv_g(Lat d, const XyFft F, c
         X[3] = mk<double>(-h * (double)f0.x, h * (double)f0.y);  // -conj(Delta01)
         X[4] = mk<double>(1.0, h * (double)f3.y);
         X[5] = mk<double>(h * (double)f2.x, h * (double)f2.y);
-        cx<double> gm[9];
-        reunit_rows(X, gm);
+        // Gram-Schmidt in FP64; row 2 = conj(r0 x r1) in the precision g is
+        // stored in (for an FP32 g, from the rounded rows, so that the stored g
+        // is unitary to FP32 rounding)
+        cx<double> gm[6];
+        gram_schmidt01(X, gm);
+        cx<TG> gs[9];
 #pragma unroll
-        for (int e = 0; e < 9; e++) {
-            vec2_t<TG> v;
-            v.x = (TG)gm[e].re;
-            v.y = (TG)gm[e].im;
-            g[(size_t)e * V + s0 + xy] = v;
-        }
+        for (int e = 0; e < 6; e++) gs[e] = mk<TG>((TG)gm[e].re, (TG)gm[e].im);
+        complete_row2(gs, gs + 6);
+#pragma unroll
+        for (int e = 0; e < 9; e++) st<TG>(g + (size_t)e * V + s0 + xy, gs[e]);
     }
 }
 
@@ -304,7 +342,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_xyinv_g(Lat d, const XyFft F, c
 
 // One thread per site.  G may be null (gauge not tracked).
 template <typename T>
-__global__ void __launch_bounds__(256) k_update(Lat d, vec2_t<T>* __restrict__ U, vec2_t<T>* __restrict__ G,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, vec2_t<T>* __restrict__ U, vec2_t<T>* __restrict__ G,
                                                const vec2_t<T>* __restrict__ g, Ctl* ctl)
 {
     if (ld_flag(&ctl->phase_done)) return;

@@ -16,6 +16,8 @@ struct Tables {
     const float2* tw32[4];
     const double* s2[4];
     double p2max;
+    const double* mult64;  // p2max/(p2(k) V) per momentum, or null (then computed in the kernel)
+    const float* mult32;
 };
 
 // launch shape and FFT plans of the plane-tiled kernels of one precision
@@ -51,6 +53,7 @@ void launch_mixed_prep(cudaStream_t s, int V, const double2* U64, float2* U32, f
 void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
                    Ctl* ctl);
 void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h);
+void launch_make_mult(cudaStream_t s, const Lat& d, const Tables& tb, double* m64, float* m32);
 // derivative of one step and of the gluon propagator (lgf_diff.cuh)
 void launch_g_from_dt(cudaStream_t s, int V, const double2* Fd, double2* g, double alpha);
 void launch_pack_full(cudaStream_t s, int V, const double* in, double2* out);

@@ -6,6 +6,10 @@
 
 namespace lgf {
 
+template <typename T> inline const T* mult_of(const Tables& tb);
+template <> inline const double* mult_of<double>(const Tables& tb) { return tb.mult64; }
+template <> inline const float* mult_of<float>(const Tables& tb) { return tb.mult32; }
+
 template <typename T> inline const vec2_t<T>* tw_of(const Tables& tb, int mu);
 template <> inline const double2* tw_of<double>(const Tables& tb, int mu) { return tb.tw64[mu]; }
 template <> inline const float2* tw_of<float>(const Tables& tb, int mu) { return tb.tw32[mu]; }
@@ -63,8 +67,9 @@ template <typename T>
 void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl)
 {
     dim3 grid(d.L[0] / sh.zt.xw, d.L[1], 4);
-    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.zt, Fd, ctl, tw_of<T>(tb, 2), tw_of<T>(tb, 3), tb.s2[0],
-                                                      tb.s2[1], tb.s2[2], tb.s2[3], tb.p2max);
+    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.zt, Fd, ctl, tw_of<T>(tb, 2), tw_of<T>(tb, 3),
+                                                      mult_of<T>(tb), tb.s2[0], tb.s2[1], tb.s2[2], tb.s2[3],
+                                                      tb.p2max);
 }
 
 template <typename T>
