@@ -112,6 +112,15 @@ int lgf_get_history(lgf_ctx* ctx, double* theta_F, int n_max, int* written);
 /* lgf_stats: phase split of the last lgf_fix (iterations in the FP32 phase). */
 int lgf_get_stats(lgf_ctx* ctx, int* iters_fp32, int* iters_fp64);
 
+/*
+ * lgf_set_loop_bound (fault injection for tests): cap each device-side loop of
+ * later lgf_fix calls at max_body_runs executions of its body.  A loop ended by
+ * the cap before its stop condition makes lgf_fix return LGF_ERR_TIMEOUT, the
+ * status the safety bound (max_iter + 2 body runs) would give.  0 removes the
+ * cap (the default).
+ */
+int lgf_set_loop_bound(lgf_ctx* ctx, int max_body_runs);
+
 /* Threshold on theta that ends the FP32 phase of LGF_MIXED (default 1e-6). */
 int lgf_set_switch_tol(lgf_ctx* ctx, double switch_tol);
 

@@ -87,6 +87,7 @@ struct lgf_ctx {
     Ctl* host_ctl = nullptr;  // pinned
     bool have_links = false;
     double switch_tol = 1e-6;
+    unsigned int loop_bound = 0;  // test hook: cap on loop-body runs
     cudaGraphExec_t exec = nullptr;
     int last_iters = 0, last_iters32 = 0, last_hist = 0;
     // workspace of the derivative entry points (allocated on first use)
@@ -648,6 +649,7 @@ Ctl initial_ctl(const lgf_ctx* c, double alpha, double tol, int max_iter)
     h.max_iter = max_iter;
     h.phase = c->mixed ? 0 : 1;
     h.hist_cap = kHistCap;
+    h.loop_bound = c->loop_bound;
     return h;
 }
 
@@ -712,6 +714,13 @@ int lgf_set_stream(lgf_ctx* c, void* stream)
 {
     if (!c) return LGF_ERR_ARG;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
+    return LGF_OK;
+}
+
+int lgf_set_loop_bound(lgf_ctx* c, int max_body_runs)
+{
+    if (!c || max_body_runs < 0) return LGF_ERR_ARG;
+    c->loop_bound = (unsigned int)max_body_runs;
     return LGF_OK;
 }
 

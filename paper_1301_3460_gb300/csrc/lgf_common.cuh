@@ -153,7 +153,7 @@ struct Ctl {
     unsigned int ticket;   // last-block counter of the reduction
     unsigned int body_runs;
     int hist_cap;
-    int pad;
+    unsigned int loop_bound;  // extra cap on body runs of a device loop (0: none)
 };
 
 }  // namespace lgf

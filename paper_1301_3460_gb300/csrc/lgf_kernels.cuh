@@ -411,7 +411,9 @@ static __global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h, unsign
 {
     unsigned int n = ctl->body_runs + 1u;
     ctl->body_runs = n;
-    const int cont = !ld_flag(&ctl->phase_done) && n < bound && n < (unsigned int)ctl->max_iter + 2u;
+    const unsigned int cap = ctl->loop_bound;
+    const int cont = !ld_flag(&ctl->phase_done) && n < bound && n < (unsigned int)ctl->max_iter + 2u &&
+                     (cap == 0u || n < cap);
     cudaGraphSetConditional(h, cont ? 1u : 0u);
 }
 

@@ -77,6 +77,7 @@ def load(build_if_missing: bool = True):
             "lgf_get_history": ([P, DP, I, IP], I),
             "lgf_get_stats": ([P, IP, IP], I),
             "lgf_set_switch_tol": ([P, D], I),
+            "lgf_set_loop_bound": ([P, I], I),
             "lgf_delta": ([P, P, I, DP, DP], I),
             "lgf_accelerate": ([P, P, P, I], I),
             "lgf_build_g": ([P, P, D, P, I], I),
@@ -180,6 +181,10 @@ class Lattice:
         """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default)."""
         raw = getattr(stream, "cuda_stream", stream)
         _check(self._lib.lgf_set_stream(self._h, ctypes.c_void_p(raw or 0)), "lgf_set_stream")
+
+    def set_loop_bound(self, n: int):
+        """Fault injection: cap each device loop at n body runs (0: no cap)."""
+        _check(self._lib.lgf_set_loop_bound(self._h, int(n)), "lgf_set_loop_bound")
 
     def set_switch_tol(self, tol: float):
         _check(self._lib.lgf_set_switch_tol(self._h, float(tol)), "lgf_set_switch_tol")

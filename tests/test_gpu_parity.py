@@ -196,3 +196,20 @@ def test_contexts_of_different_sizes_coexist():
     finally:
         big.close()
         small.close()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_device_loop_cap_reports_timeout(mixed):
+    """Host-side fault injection: a device loop stopped by its body-run cap before
+    its stop condition is reported as LGF_ERR_TIMEOUT, and the context stays usable."""
+    L = (8, 8, 8, 8)
+    U = field(L, seed=13)
+    with lgf.Lattice(L, mixed=mixed) as lat:
+        lat.set_links(U)
+        lat.set_loop_bound(3)
+        r = lat.fix(tol=1e-15, max_iter=1000, check=False)
+        assert r["status"] == lgf.LGF_ERR_TIMEOUT
+        lat.set_loop_bound(0)
+        lat.set_links(U)
+        r = lat.fix(tol=1e-15, max_iter=1000)
+        assert r["converged"]
