@@ -75,6 +75,10 @@ struct lgf_ctx {
     float2* G32 = nullptr;
     float2* g32 = nullptr;
     void* Fd = nullptr;       // [4][V] double2 (the FP32 phase uses the front half as float2)
+    double2* AH64 = nullptr;  // [4][4][V] packed anti-Hermitian parts of the links
+    double* Fs64 = nullptr;   // [V] Re Tr of the four links of a site
+    float2* AH32 = nullptr;
+    float* Fs32 = nullptr;
     double* partials = nullptr;
     Ctl* ctl = nullptr;       // loop state of lgf_fix
     Ctl* ctl_stage = nullptr; // state used by the stage entry points
@@ -144,6 +148,13 @@ bool pick_shape(const Lat& d, size_t elem, int prefer_nfc, int prefer_xw, Shape*
     return false;
 }
 
+template <typename T> vec2_t<T>* ah_of(lgf_ctx* c);
+template <> double2* ah_of<double>(lgf_ctx* c) { return c->AH64; }
+template <> float2* ah_of<float>(lgf_ctx* c) { return c->AH32; }
+template <typename T> T* fs_of(lgf_ctx* c);
+template <> double* fs_of<double>(lgf_ctx* c) { return c->Fs64; }
+template <> float* fs_of<float>(lgf_ctx* c) { return c->Fs32; }
+
 template <typename T> const Shape& shape_of(const lgf_ctx* c);
 template <> const Shape& shape_of<double>(const lgf_ctx* c) { return c->sh64; }
 template <> const Shape& shape_of<float>(const lgf_ctx* c) { return c->sh32; }
@@ -156,8 +167,8 @@ void launch_body(lgf_ctx* c, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, vec2_t<
     const Shape& sh = shape_of<T>(c);
     launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl);
     launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g, c->ctl);
-    launch_update<T>(c->lat, s, U, G, g, c->ctl);
-    launch_delta<T>(c->lat, sh, c->tb, s, U, Fd, c->partials, c->ctl, c->hist, true);
+    launch_update<T>(c->lat, s, U, G, g, c->ctl, ah_of<T>(c), fs_of<T>(c));
+    launch_delta<T>(c->lat, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl, c->hist, true);
 }
 
 // ---------------------------------------------------------------- graph
@@ -221,18 +232,23 @@ int append_fix(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps
     if (c->mixed) {
         CKR(capture_begin(c, graph, deps));
         launch_mixed_prep(c->cap, c->V, c->U64, c->U32, c->G32, c->ctl);
-        launch_delta<float>(c->lat, c->sh32, c->tb, c->cap, c->U32, reinterpret_cast<float2*>(c->Fd), c->partials,
-                            c->ctl, c->hist, true);
+        launch_ah_init<float>(c->lat, c->cap, c->U32, c->AH32, c->Fs32);
+        launch_delta<float>(c->lat, c->sh32, c->tb, c->cap, c->AH32, c->Fs32, reinterpret_cast<float2*>(c->Fd),
+                            c->partials, c->ctl, c->hist, true);
         CKR(capture_end(c, deps));
         CKR(add_loop<float>(c, graph, deps, c->U32, c->G32, c->g32));
         CKR(capture_begin(c, graph, deps));
         launch_switch(c->cap, c->lat, c->G32, c->g64, c->U64, c->G64, c->ctl);
-        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->U64, Fd64, c->partials, c->ctl, c->hist, true);
+        launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
+        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
+                             true);
         CKR(capture_end(c, deps));
         CKR(add_loop<double>(c, graph, deps, c->U64, c->G64, c->g64));
     } else {
         CKR(capture_begin(c, graph, deps));
-        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->U64, Fd64, c->partials, c->ctl, c->hist, true);
+        launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
+        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
+                             true);
         CKR(capture_end(c, deps));
         CKR(add_loop<double>(c, graph, deps, c->U64, c->track ? c->G64 : nullptr, c->g64));
     }
@@ -373,7 +389,11 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     if (c->track) CKR(alloc((void**)&c->G64, 6 * Vs * sizeof(double2)));
     CKR(alloc((void**)&c->g64, 9 * Vs * sizeof(double2)));
     CKR(alloc(&c->Fd, 4 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->AH64, 16 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->Fs64, Vs * sizeof(double)));
     if (c->mixed) {
+        CKR(alloc((void**)&c->AH32, 16 * Vs * sizeof(float2)));
+        CKR(alloc((void**)&c->Fs32, Vs * sizeof(float)));
         CKR(alloc((void**)&c->U32, 24 * Vs * sizeof(float2)));
         CKR(alloc((void**)&c->G32, 6 * Vs * sizeof(float2)));
         CKR(alloc((void**)&c->g32, 9 * Vs * sizeof(float2)));
@@ -394,7 +414,7 @@ void free_all(lgf_ctx* c)
 {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
-                    c->hist, c->err, c->stage, c->tables, c->mult, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
+                    c->hist, c->err, c->stage, c->tables, c->mult, c->AH64, c->Fs64, c->AH32, c->Fs32, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
                     c->gl_part, c->gl_At, c->gl_D};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -460,9 +480,6 @@ template <typename T> Shape& shape_ref(lgf_ctx* c);
 template <> Shape& shape_ref<double>(lgf_ctx* c) { return c->sh64; }
 template <> Shape& shape_ref<float>(lgf_ctx* c) { return c->sh32; }
 
-template <typename T> vec2_t<T>* links_of(lgf_ctx* c);
-template <> double2* links_of<double>(lgf_ctx* c) { return c->U64; }
-template <> float2* links_of<float>(lgf_ctx* c) { return c->U32; }
 template <typename T> vec2_t<T>* g_of(lgf_ctx* c);
 template <> double2* g_of<double>(lgf_ctx* c) { return c->g64; }
 template <> float2* g_of<float>(lgf_ctx* c) { return c->g32; }
@@ -479,7 +496,8 @@ template <typename T> int time_shape(lgf_ctx* c, const Shape& sh, int which, flo
     for (int r = 0; r <= reps; r++) {
         if (r == 1) cudaEventRecord(e0, s);
         if (which == 0) {
-            launch_delta<T>(c->lat, sh, c->tb, s, links_of<T>(c), Fd, c->partials, c->ctl_stage, nullptr, true);
+            launch_delta<T>(c->lat, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl_stage, nullptr,
+                            true);
             launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g_of<T>(c), c->ctl_stage);
         } else {
             launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl_stage);
@@ -549,9 +567,11 @@ int autotune_ctx(lgf_ctx* c)
 {
     if (!c->have_links) return LGF_ERR_STATE;
     CKR(reset_stage_ctl(c, 0.08));
+    launch_ah_init<double>(c->lat, c->stream, c->U64, c->AH64, c->Fs64);
     CKR(autotune_prec<double>(c));
     if (c->mixed) {
         launch_mixed_prep(c->stream, c->V, c->U64, c->U32, c->G32, c->ctl_stage);
+        launch_ah_init<float>(c->lat, c->stream, c->U32, c->AH32, c->Fs32);
         CKR(autotune_prec<float>(c));
     }
     CK(cudaStreamSynchronize(c->stream));
@@ -827,7 +847,9 @@ int lgf_delta(lgf_ctx* c, double* Delta_out, int on_device, double* theta, doubl
     if (!c->have_links) return LGF_ERR_STATE;
     CKR(reset_stage_ctl(c));
     double2* Fd = reinterpret_cast<double2*>(c->Fd);
-    launch_delta<double>(c->lat, c->sh64, c->tb, c->stream, c->U64, Fd, c->partials, c->ctl_stage, nullptr, false);
+    launch_ah_init<double>(c->lat, c->stream, c->U64, c->AH64, c->Fs64);
+    launch_delta<double>(c->lat, c->sh64, c->tb, c->stream, c->AH64, c->Fs64, Fd, c->partials, c->ctl_stage, nullptr,
+                         false);
     CK(cudaGetLastError());
     if (Delta_out) {
         const size_t bytes = (size_t)c->V * 18 * sizeof(double);
@@ -899,27 +921,35 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
     double acc[4] = {0, 0, 0, 0};
     cudaStream_t s = c->stream;
     int rc = LGF_OK;
-    if (precision == 32) launch_mixed_prep(s, c->V, c->U64, c->U32, c->G32, c->ctl_stage);
+    if (precision == 32) {
+        launch_mixed_prep(s, c->V, c->U64, c->U32, c->G32, c->ctl_stage);
+        launch_ah_init<float>(c->lat, s, c->U32, c->AH32, c->Fs32);
+    } else {
+        launch_ah_init<double>(c->lat, s, c->U64, c->AH64, c->Fs64);
+    }
     for (int it = 0; it < n_iter && rc == LGF_OK; it++) {
         cudaEventRecord(ev[0], s);
         if (precision == 64) {
             double2* Fd = reinterpret_cast<double2*>(c->Fd);
-            launch_delta<double>(c->lat, c->sh64, c->tb, s, c->U64, Fd, c->partials, c->ctl_stage, nullptr, true);
+            launch_delta<double>(c->lat, c->sh64, c->tb, s, c->AH64, c->Fs64, Fd, c->partials, c->ctl_stage, nullptr,
+                                 true);
             cudaEventRecord(ev[1], s);
             launch_zt<double>(c->lat, c->sh64, c->tb, s, Fd, c->ctl_stage);
             cudaEventRecord(ev[2], s);
             launch_xyinv_g<double>(c->lat, c->sh64, c->tb, s, Fd, c->g64, c->ctl_stage);
             cudaEventRecord(ev[3], s);
-            launch_update<double>(c->lat, s, c->U64, c->track ? c->G64 : nullptr, c->g64, c->ctl_stage);
+            launch_update<double>(c->lat, s, c->U64, c->track ? c->G64 : nullptr, c->g64, c->ctl_stage, c->AH64,
+                                  c->Fs64);
         } else {
             float2* Fd = reinterpret_cast<float2*>(c->Fd);
-            launch_delta<float>(c->lat, c->sh32, c->tb, s, c->U32, Fd, c->partials, c->ctl_stage, nullptr, true);
+            launch_delta<float>(c->lat, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, c->ctl_stage, nullptr,
+                                true);
             cudaEventRecord(ev[1], s);
             launch_zt<float>(c->lat, c->sh32, c->tb, s, Fd, c->ctl_stage);
             cudaEventRecord(ev[2], s);
             launch_xyinv_g<float>(c->lat, c->sh32, c->tb, s, Fd, c->g32, c->ctl_stage);
             cudaEventRecord(ev[3], s);
-            launch_update<float>(c->lat, s, c->U32, c->G32, c->g32, c->ctl_stage);
+            launch_update<float>(c->lat, s, c->U32, c->G32, c->g32, c->ctl_stage, c->AH32, c->Fs32);
         }
         cudaEventRecord(ev[4], s);
         cudaError_t e = cudaEventSynchronize(ev[4]);
@@ -1085,7 +1115,8 @@ int lgf_step_bwd(lgf_ctx* c, double alpha, const double* gU_out, double* gU_in)
     cudaStream_t s = c->stream;
     double2* Fd = reinterpret_cast<double2*>(c->Fd);
     // forward of the step on the stored links, up to g and the spatial Delta~
-    launch_delta<double>(c->lat, c->sh64, c->tb, s, c->U64, Fd, c->partials, c->ctl_stage, nullptr, true);
+    launch_ah_init<double>(c->lat, s, c->U64, c->AH64, c->Fs64);
+    launch_delta<double>(c->lat, c->sh64, c->tb, s, c->AH64, c->Fs64, Fd, c->partials, c->ctl_stage, nullptr, true);
     launch_zt<double>(c->lat, c->sh64, c->tb, s, Fd, c->ctl_stage);
     launch_xy_fft<double>(c->lat, c->sh64, c->tb, s, Fd, true);
     launch_g_from_dt(s, c->V, Fd, c->g64, alpha);

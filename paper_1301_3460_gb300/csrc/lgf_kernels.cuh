@@ -1,13 +1,15 @@
 // Kernels of one Fourier-accelerated steepest-descent iteration (arXiv:1301.3460):
 //
 //   k_delta      Delta(x) = (M - M^dag) - Tr(M - M^dag)/3, M = sum_mu [U_mu(x-mu) - U_mu(x)],
-//                packed into four complex fields, theta and F reduced in FP64, then
-//                the forward FFT along x and y of the xy-plane.
+//                packed into four complex fields (as sums of the links' packed
+//                anti-Hermitian parts), theta and F reduced in FP64, then the
+//                forward FFT along x and y of the xy-plane.
 //   k_zt         forward FFT along z and t, the accelerator p2max/(p2(k) V)
 //                (zero mode removed), inverse FFT along t and z.
 //   k_xyinv_g    inverse FFT along x and y, then g(x) = reunit(1 + alpha/2 Delta~(x))
 //                by row Gram-Schmidt in FP64.
-//   k_update     U_mu(x) <- g(x) U_mu(x) g^dag(x+mu) and G(x) <- g(x) G(x).
+//   k_update     U_mu(x) <- g(x) U_mu(x) g^dag(x+mu) and G(x) <- g(x) G(x); writes the
+//                packed anti-Hermitian parts and Re Tr of the new links for k_delta.
 //
 // Storage (structure of arrays, one plane of V complex numbers per entry):
 //   links U  [mu=4][e=6][V]  rows 0,1 of U_mu(x), e = 3 i + j; row 2 is rebuilt
@@ -118,12 +120,51 @@ __device__ __forceinline__ void load_g(const vec2_t<T>* __restrict__ g, int V, i
 
 // ---------------------------------------------------------------- k_delta
 
-// One block per xy-plane.  Shared memory: (4 + nfc) * P complex values.  FFT = false
-// stores the packed Delta itself (used to check the stencil on its own).
+// The traceless anti-Hermitian part of one link w (full matrix), packed as four
+// complex numbers in the layout of the Delta fields: w01 - conj(w10),
+// w02 - conj(w20), w12 - conj(w21), and 2 (Im w00 - t) + 2 i (Im w11 - t) with
+// t = (Im w00 + Im w11 + Im w22)/3.  Delta(x) is linear in the links, so it is
+// the sum over mu of ah(U_mu(x - mu)) - ah(U_mu(x)).
+template <typename T> __device__ __forceinline__ void ah_pack(const cx<T>* w, cx<T>* a)
+{
+    a[0] = w[1] - conjg(w[3]);
+    a[1] = w[2] - conjg(w[6]);
+    a[2] = w[5] - conjg(w[7]);
+    const T t = (w[0].im + w[4].im + w[8].im) * (T)(1.0 / 3.0);
+    a[3] = mk<T>((T)2 * (w[0].im - t), (T)2 * (w[4].im - t));
+}
+
+// ah of every link and the per-site sum of Re Tr over the four links, from
+// links whose row 2 is rebuilt (before the first iteration; the update kernel
+// writes them for the links it produces).  AH: [mu=4][k=4][V], Fs: [V].
+template <typename T>
+__global__ void __launch_bounds__(256) k_ah_init(Lat d, const vec2_t<T>* __restrict__ U, vec2_t<T>* __restrict__ AH,
+                                                 T* __restrict__ Fs)
+{
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    T f = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        cx<T> u[9], a[4];
+        load_link<T>(U, V, mu, s, u);
+        ah_pack(u, a);
+#pragma unroll
+        for (int k = 0; k < 4; k++) st<T>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
+        f += u[0].re + u[4].re + u[8].re;
+    }
+    Fs[s] = f;
+}
+
+// One block per xy-plane.  Shared memory: (4 + nfc) * P complex values.
+// Delta(x) = sum_mu ah_mu(x - mu) - ah_mu(x) (packed fields), theta and F
+// reduced in FP64, then (FFT = true) the forward FFT along x and y.
 template <typename T, bool FFT>
-__global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, const vec2_t<T>* __restrict__ U,
-                                                       vec2_t<T>* __restrict__ Fd, double* __restrict__ partials,
-                                                       Ctl* ctl, double2* hist, const vec2_t<T>* __restrict__ twx,
+__global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, const vec2_t<T>* __restrict__ AH,
+                                                       const T* __restrict__ Fs, vec2_t<T>* __restrict__ Fd,
+                                                       double* __restrict__ partials, Ctl* ctl, double2* hist,
+                                                       const vec2_t<T>* __restrict__ twx,
                                                        const vec2_t<T>* __restrict__ twy)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,40 +179,23 @@ __global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, con
         const int s = s0 + xy;
         const int x = xy % d.L[0], y = xy / d.L[0];
         const int c[4] = {x, y, z, t};
-        cx<T> M[9];
+        cx<T> D[4];
 #pragma unroll
-        for (int e = 0; e < 9; e++) M[e] = mk<T>(0, 0);
-        T tr = 0;
+        for (int k = 0; k < 4; k++) D[k] = mk<T>(0, 0);
 #pragma unroll
         for (int mu = 0; mu < 4; mu++) {
-            cx<T> u[9];
-            load_link<T>(U, V, mu, s, u);
-            tr += u[0].re + u[4].re + u[8].re;
-#pragma unroll
-            for (int e = 0; e < 9; e++) M[e] = M[e] - u[e];
             const int sb = site_shift(d, s, c[mu], mu, -1);
-            load_link<T>(U, V, mu, sb, u);
 #pragma unroll
-            for (int e = 0; e < 9; e++) M[e] = M[e] + u[e];
+            for (int k = 0; k < 4; k++)
+                D[k] = D[k] + ld<T>(AH + (size_t)(mu * 4 + k) * V + sb) - ld<T>(AH + (size_t)(mu * 4 + k) * V + s);
         }
-        fsum += (double)tr;
-        // Delta_ij = M_ij - conj(M_ji); diagonal: 2 i Im M_ii minus a third of the trace
-        cx<T> d01 = M[1] - conjg(M[3]);
-        cx<T> d02 = M[2] - conjg(M[6]);
-        cx<T> d12 = M[5] - conjg(M[7]);
-        const T third = (T)(1.0 / 3.0);
-        const T trI = (M[0].im + M[4].im + M[8].im) * third;
-        const T a = (T)2 * (M[0].im - trI);
-        const T b = (T)2 * (M[4].im - trI);
-        const T cc = a + b;
+        fsum += (double)__ldg(Fs + s);
+        const T a = D[3].re, b = D[3].im, cc = a + b;
         // per-site sum of |Delta_ij|^2 in the kernel's precision, accumulated over
         // sites in FP64
-        th += (double)((T)2 * (norm2(d01) + norm2(d02) + norm2(d12)) + a * a + b * b + cc * cc);
-        vec2_t<T> v;
-        v.x = d01.re; v.y = d01.im; sm[xy] = v;
-        v.x = d02.re; v.y = d02.im; sm[P + xy] = v;
-        v.x = d12.re; v.y = d12.im; sm[2 * P + xy] = v;
-        v.x = a; v.y = b; sm[3 * P + xy] = v;
+        th += (double)((T)2 * (norm2(D[0]) + norm2(D[1]) + norm2(D[2])) + a * a + b * b + cc * cc);
+#pragma unroll
+        for (int k = 0; k < 4; k++) st<T>(sm + k * P + xy, D[k]);
     }
     reduce_theta_F(th, fsum, partials, ctl, hist, V);
     __syncthreads();
@@ -340,10 +364,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_xyinv_g(Lat d, const XyFft F, c
 
 // ---------------------------------------------------------------- k_update
 
-// One thread per site.  G may be null (gauge not tracked).
+// One thread per site.  G may be null (gauge not tracked).  Also writes the
+// packed anti-Hermitian parts of the new links (AH) and their Re Tr per site
+// (Fs) for the next Delta.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, vec2_t<T>* __restrict__ U, vec2_t<T>* __restrict__ G,
-                                               const vec2_t<T>* __restrict__ g, Ctl* ctl)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, vec2_t<T>* __restrict__ U,
+                                                                        vec2_t<T>* __restrict__ G,
+                                                                        const vec2_t<T>* __restrict__ g, Ctl* ctl,
+                                                                        vec2_t<T>* __restrict__ AH,
+                                                                        T* __restrict__ Fs)
 {
     if (ld_flag(&ctl->phase_done)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -357,6 +386,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
     site_coords(d, s, c);
     cx<T> gx[9];
     load_g<T>(g, V, s, gx);
+    T f = 0;
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         cx<T> u[9];
@@ -374,7 +404,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
             }
         cx<T> gn[9];
         load_g<T>(g, V, site_shift(d, s, c[mu], mu, +1), gn);
-        // U' = A g^dag(x+mu): U'_ij = sum_k A_ik conj(gn_jk)
+        // U' = A g^dag(x+mu): U'_ij = sum_k A_ik conj(gn_jk); row 2 rebuilt
+        cx<T> w[9];
 #pragma unroll
         for (int i = 0; i < 2; i++)
 #pragma unroll
@@ -382,9 +413,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
                 cx<T> acc = cmulc(A[3 * i], gn[3 * j]);
                 acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
                 acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
+                w[3 * i + j] = acc;
                 st<T>(U + (size_t)(mu * 6 + 3 * i + j) * V + s, acc);
             }
+        complete_row2(w, w + 6);
+        cx<T> a[4];
+        ah_pack(w, a);
+#pragma unroll
+        for (int k = 0; k < 4; k++) st<T>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
+        f += w[0].re + w[4].re + w[8].re;
     }
+    Fs[s] = f;
     if (G != nullptr) {
         cx<T> Gm[9];
 #pragma unroll

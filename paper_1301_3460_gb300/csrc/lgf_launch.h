@@ -30,8 +30,9 @@ struct Shape {
 
 template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh);
 template <typename T>
-void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* U,
+void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* AH, const T* Fs,
                   vec2_t<T>* Fd, double* partials, Ctl* ctl, double2* hist, bool fft);
+template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const vec2_t<T>* U, vec2_t<T>* AH, T* Fs);
 template <typename T>
 void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl);
 template <typename T>
@@ -40,7 +41,8 @@ void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_
 template <typename T>
 void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, bool inv);
 template <typename T>
-void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, const vec2_t<T>* g, Ctl* ctl);
+void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, const vec2_t<T>* g, Ctl* ctl,
+                   vec2_t<T>* AH, T* Fs);
 
 // conversion, checking and mode-switch kernels (FP64 unit)
 void launch_pack_links64(cudaStream_t s, int V, const double* in, double2* U, unsigned long long* err);

@@ -51,16 +51,21 @@ template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh)
 }
 
 template <typename T>
-void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* U,
+void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* AH, const T* Fs,
                   vec2_t<T>* Fd, double* partials, Ctl* ctl, double2* hist, bool fft)
 {
     const size_t sm = xy_smem<T>(d, sh);
     if (fft)
-        k_delta<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, U, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
+        k_delta<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, AH, Fs, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
                                                          tw_of<T>(tb, 1));
     else
-        k_delta<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, U, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
+        k_delta<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, AH, Fs, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
                                                           tw_of<T>(tb, 1));
+}
+
+template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const vec2_t<T>* U, vec2_t<T>* AH, T* Fs)
+{
+    k_ah_init<T><<<(d.V + 255) / 256, 256, 0, s>>>(d, U, AH, Fs);
 }
 
 template <typename T>
@@ -91,19 +96,22 @@ void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t
 }
 
 template <typename T>
-void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, const vec2_t<T>* g, Ctl* ctl)
+void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, const vec2_t<T>* g, Ctl* ctl,
+                   vec2_t<T>* AH, T* Fs)
 {
-    k_update<T><<<(d.V + 255) / 256, 256, 0, s>>>(d, U, G, g, ctl);
+    k_update<T><<<(d.V + 255) / 256, 256, 0, s>>>(d, U, G, g, ctl, AH, Fs);
 }
 
 #define LGF_INSTANTIATE(T)                                                                                        \
     template cudaError_t prepare_kernels<T>(const Lat&, const Shape&);                                           \
     template void launch_delta<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, const vec2_t<T>*,       \
-                                  vec2_t<T>*, double*, Ctl*, double2*, bool);                                     \
+                                  const T*, vec2_t<T>*, double*, Ctl*, double2*, bool);                           \
+    template void launch_ah_init<T>(const Lat&, cudaStream_t, const vec2_t<T>*, vec2_t<T>*, T*);                  \
     template void launch_zt<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, vec2_t<T>*, const Ctl*);    \
     template void launch_xyinv_g<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, const vec2_t<T>*,     \
                                     vec2_t<T>*, const Ctl*);                                                      \
     template void launch_xy_fft<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, vec2_t<T>*, bool);      \
-    template void launch_update<T>(const Lat&, cudaStream_t, vec2_t<T>*, vec2_t<T>*, const vec2_t<T>*, Ctl*);
+    template void launch_update<T>(const Lat&, cudaStream_t, vec2_t<T>*, vec2_t<T>*, const vec2_t<T>*, Ctl*,       \
+                                   vec2_t<T>*, T*);
 
 }  // namespace lgf

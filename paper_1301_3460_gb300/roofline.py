@@ -6,19 +6,22 @@ multiplies/adds (an FMA is 2), with the FFT at the conventional 5 N log2 N per
 complex transform of length N.
 
 FP64 path, per site (V sites per launch):
-  delta_xyfft   reads the links (4 x 12 reals, rows 0,1) and writes the four
-                packed Delta fields: 384 + 64 B.  Flops: rebuild row 2 of 8
-                links (8 x 42), M (8 x 9 complex adds = 144), Delta, theta, F
-                (46), x,y FFT of 4 fields (4 x 5 log2(Lx Ly)).
-  zt_fft_accel  reads and writes the 4 fields: 64 + 64 B.  Flops: forward and
-                inverse z,t FFT of 4 fields (2 x 4 x 5 log2(Lz Lt)) + scale (8).
+  delta_xyfft   reads the packed anti-Hermitian parts of the four links (4 x 4
+                complex) and their Re Tr sum, writes the four packed Delta
+                fields: 256 + 8 + 64 B.  Flops: Delta as 16 complex differences
+                (64), theta and F (21), x,y FFT of 4 fields (4 x 5 log2(Lx Ly)).
+  zt_fft_accel  reads the multiplier and reads/writes the 4 fields: 8 + 64 + 64 B.
+                Flops: forward and inverse z,t FFT of 4 fields
+                (2 x 4 x 5 log2(Lz Lt)) + scale (8).
   xyifft_g      reads the 4 fields, writes g (full 3x3): 64 + 144 B.  Flops:
                 inverse x,y FFT (4 x 5 log2(Lx Ly)) + Gram-Schmidt and row 2 (134).
-  update        reads links, g, G; writes links and G: 384 + 144 + 96 + 384 + 96 B.
-                Flops: per link row-2 rebuild (42) and two 2x3 by 3x3 complex
-                products (2 x 132); G: rebuild (42) + one product (132).
+  update        reads links, g, G; writes links, G, the packed anti-Hermitian
+                parts and Re Tr: 384 + 144 + 96 + 384 + 96 + 256 + 8 B.  Flops:
+                per link row-2 rebuild (42), two 2x3 by 3x3 complex products
+                (2 x 132), row 2 of the result (42), packing (12), Re Tr (2);
+                G: rebuild (42) + one product (132).
 FP32 kernels move half the bytes of every array they keep in FP32 (links, G, g,
-fields); their flop counts are the same.
+fields, packed parts, multiplier); their flop counts are the same.
 """
 from __future__ import annotations
 
@@ -33,10 +36,11 @@ def per_site(dims, precision: int = 64) -> dict:
     lxy = math.log2(Lx * Ly)
     lzt = math.log2(Lz * Lt)
     return {
-        "delta_xyfft": dict(bytes=(384 + 64) * w, flops=8 * 42 + 144 + 46 + 4 * 5 * lxy),
-        "zt_fft_accel": dict(bytes=(64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
+        "delta_xyfft": dict(bytes=(256 + 8 + 64) * w, flops=64 + 21 + 4 * 5 * lxy),
+        "zt_fft_accel": dict(bytes=(8 + 64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
         "xyifft_g": dict(bytes=(64 + 144) * w, flops=4 * 5 * lxy + 134),
-        "update": dict(bytes=(384 + 144 + 96 + 384 + 96) * w, flops=4 * (42 + 2 * 132) + 42 + 132),
+        "update": dict(bytes=(384 + 144 + 96 + 384 + 96 + 256 + 8) * w,
+                       flops=4 * (42 + 2 * 132 + 42 + 12 + 2) + 42 + 132),
     }
 
 
