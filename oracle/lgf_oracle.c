@@ -411,13 +411,16 @@ void orc_gauge_transform(const int L[4], const cplx* U, const cplx* G, cplx* Uou
 /* the iteration                                                        */
 /* ------------------------------------------------------------------ */
 
-/* Fourier-accelerated steepest descent.  U (in/out) holds the links, G (in/out,
- * may be NULL) accumulates the applied gauge transformation.  The stop test is
- * made on the current links before an update: the run ends when theta < tol or
- * when max_iter updates have been applied.  history, if not NULL, receives
- * (theta_n, F_n) for n = 0..iters.  Returns 0 if converged, 1 if not. */
-int orc_fix(const int L[4], cplx* U, cplx* G, double alpha, double tol, int max_iter, int use_dft,
-            int* iters, double* F, double* theta, double* history)
+/* Steepest descent, Fourier-accelerated (accel = 1) or plain (accel = 0: the
+ * step uses Delta itself, the unaccelerated method whose critical slowing down
+ * the introduction names as the reason for Fourier acceleration).  U (in/out)
+ * holds the links, G (in/out, may be NULL) accumulates the applied gauge
+ * transformation.  The stop test is made on the current links before an
+ * update: the run ends when theta < tol or when max_iter updates have been
+ * applied.  history, if not NULL, receives (theta_n, F_n) for n = 0..iters.
+ * Returns 0 if converged, 1 if not. */
+int orc_fix_sd(const int L[4], cplx* U, cplx* G, double alpha, double tol, int max_iter, int use_dft, int accel,
+               int* iters, double* F, double* theta, double* history)
 {
     const long V = volume(L);
     cplx* D = malloc(sizeof(cplx) * 9 * V);
@@ -432,7 +435,10 @@ int orc_fix(const int L[4], cplx* U, cplx* G, double alpha, double tol, int max_
             history[2 * n + 1] = f;
         }
         if (th < tol || n >= max_iter) break;
-        orc_accelerate(L, D, Dt, use_dft);
+        if (accel)
+            orc_accelerate(L, D, Dt, use_dft);
+        else
+            memcpy(Dt, D, sizeof(cplx) * 9 * V);
         orc_build_g(L, Dt, alpha, g);
         orc_update(L, U, G, g);
         n++;
@@ -444,6 +450,13 @@ int orc_fix(const int L[4], cplx* U, cplx* G, double alpha, double tol, int max_
     if (F) *F = f;
     if (theta) *theta = th;
     return th < tol ? 0 : 1;
+}
+
+/* the Fourier-accelerated method */
+int orc_fix(const int L[4], cplx* U, cplx* G, double alpha, double tol, int max_iter, int use_dft,
+            int* iters, double* F, double* theta, double* history)
+{
+    return orc_fix_sd(L, U, G, alpha, tol, max_iter, use_dft, 1, iters, F, theta, history);
 }
 
 /* ------------------------------------------------------------------ */

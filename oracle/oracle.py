@@ -62,6 +62,9 @@ def _load():
             lib.orc_fix.argtypes = [_int_p, v, v, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, _int_p, _dbl_p, _dbl_p, _dbl_p]
             lib.orc_fix.restype = ctypes.c_int
+            lib.orc_fix_sd.argtypes = [_int_p, v, v, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _int_p, _dbl_p, _dbl_p, _dbl_p]
+            lib.orc_fix_sd.restype = ctypes.c_int
             lib.orc_plaquette.argtypes = [_int_p, v]
             lib.orc_plaquette.restype = ctypes.c_double
             lib.orc_gluon_pmin.argtypes = [_int_p, v, _dbl_p]
@@ -183,9 +186,11 @@ def gauge_transform(L, U, G):
     return out
 
 
-def fix(L, U, alpha=0.08, tol=1e-15, max_iter=1000, use_dft=False, track_gauge=True, history=False):
-    """Fourier-accelerated steepest descent to theta < tol or max_iter updates.
-    Returns a dict with U, G (or None), iters, F, theta, converged, history."""
+def fix(L, U, alpha=0.08, tol=1e-15, max_iter=1000, use_dft=False, track_gauge=True, history=False,
+        accelerate=True):
+    """Fourier-accelerated (accelerate=True) or plain steepest descent to
+    theta < tol or max_iter updates.  Returns a dict with U, G (or None), iters,
+    F, theta, converged, history."""
     d, V = _dims(L)
     U = _c(U, (4, V, 3, 3)).copy()
     G = None
@@ -194,9 +199,9 @@ def fix(L, U, alpha=0.08, tol=1e-15, max_iter=1000, use_dft=False, track_gauge=T
         G[:, 0, 0] = G[:, 1, 1] = G[:, 2, 2] = 1.0
     hist = np.zeros(2 * (int(max_iter) + 1), np.float64) if history else None
     it, f, th = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
-    rc = _load().orc_fix(d, _ptr(U), None if G is None else _ptr(G), float(alpha), float(tol), int(max_iter),
-                         int(bool(use_dft)), ctypes.byref(it), ctypes.byref(f), ctypes.byref(th),
-                         None if hist is None else hist.ctypes.data_as(_dbl_p))
+    rc = _load().orc_fix_sd(d, _ptr(U), None if G is None else _ptr(G), float(alpha), float(tol), int(max_iter),
+                            int(bool(use_dft)), int(bool(accelerate)), ctypes.byref(it), ctypes.byref(f),
+                            ctypes.byref(th), None if hist is None else hist.ctypes.data_as(_dbl_p))
     out = dict(U=U, G=G, iters=it.value, F=f.value, theta=th.value, converged=(rc == 0))
     if hist is not None:
         out["history"] = hist[: 2 * (it.value + 1)].reshape(-1, 2)

@@ -343,3 +343,39 @@ def test_paper_parameters_fixture():
     assert p["alpha"] == 0.08 and p["theta_tol"] == 1e-15 and p["L"] == [32, 32, 32, 32]
     # (1 - alpha p2max)^2 at the paper's alpha on any even lattice
     assert (1 - p["alpha"] * orc.p2max(p["L"])) ** 2 == pytest.approx(p["linear_theta_ratio"], rel=1e-12)
+
+
+def test_plain_sd_single_mode_contraction():
+    """Plain steepest descent (no Fourier acceleration) contracts a single
+    momentum mode k of div A by (1 - alpha p2(k)) per step: theta_1/theta_0 =
+    (1 - alpha p2(k))^2 in the linear regime, where the accelerated method gives
+    (1 - alpha p2max)^2 for every k.  A_0(x) = eps cos(2 pi x/Lx) T_3 has div A
+    in the modes +-(1,0,0,0)."""
+    L = (8, 6, 4, 4)
+    V = int(np.prod(L))
+    eps = 1e-5
+    U = inputs.unit_field(L)
+    x = np.arange(V) % L[0]
+    c = eps * np.cos(2 * np.pi * x / L[0])
+    U[0, :, 0, 0] = np.exp(0.5j * c)
+    U[0, :, 1, 1] = np.exp(-0.5j * c)
+    p2 = 4 * np.sin(np.pi / L[0]) ** 2
+    for alpha in (0.08, 0.05):
+        r = orc.fix(L, U, alpha=alpha, tol=0.0, max_iter=2, history=True, accelerate=False)
+        th = r["history"][:, 0]
+        assert th[1] / th[0] == pytest.approx((1 - alpha * p2) ** 2, rel=1e-4)
+        assert th[2] / th[1] == pytest.approx((1 - alpha * p2) ** 2, rel=1e-4)
+    r = orc.fix(L, U, alpha=0.08, tol=0.0, max_iter=1, history=True, accelerate=True)
+    th = r["history"][:, 0]
+    assert th[1] / th[0] == pytest.approx((1 - 0.08 * 16) ** 2, rel=1e-4)
+
+
+def test_plain_sd_converges_and_keeps_invariants():
+    L = (6, 6, 4, 4)
+    U0 = inputs.rough_gauge_field(L, 0.3, 71)
+    r = orc.fix(L, U0, alpha=0.1, tol=1e-15, max_iter=20000, history=True, accelerate=False)
+    assert r["converged"]
+    assert np.all(np.diff(r["history"][:, 1]) >= -1e-15)
+    assert abs(orc.plaquette(L, r["U"]) - orc.plaquette(L, U0)) < 1e-13
+    ra = orc.fix(L, U0, alpha=0.08, tol=1e-15, max_iter=20000, accelerate=True)
+    assert ra["iters"] < r["iters"]
