@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble")
     return ap.parse_args()
@@ -307,6 +308,25 @@ def run_ours(args, dims):
                                      "gflops": per32[k]["flops"] * V / msm[k] / 1e6} for k in msm}
         latm.close()
 
+    # critical slowing down: plain steepest descent against the accelerated method at 16^4
+    plain = None
+    if not args.no_plain:
+        Lp = (16, 16, 16, 16)
+        Up = torch.from_numpy(configs(Lp, rank)[1]).to("cuda")
+        plain = {"dims": list(Lp), "eps": EPS[1]}
+        for name, acc, alpha in (("accelerated", True, args.alpha), ("plain", False, 0.1)):
+            lp = lgf.Lattice(Lp, accelerate=acc, stream=stream)
+            lp.set_links(Up)
+            lp.fix(alpha, args.tol, 100000)
+            lp.set_links(Up)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = lp.fix(alpha, args.tol, 100000)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plain[name] = {"alpha": alpha, "iters": r["iters"], "ms": e0.elapsed_time(e1), "converged": r["converged"]}
+            lp.close()
+
     # differentiation: forward + backward of a K-step unroll with checkpoints and D(p_min)
     diff = None
     if not args.no_diff:
@@ -386,7 +406,7 @@ def run_ours(args, dims):
             "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol,
                        "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
                        % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
-            "time_to_theta": ttt, "mixed": mixed, "diff": diff, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "time_to_theta": ttt, "mixed": mixed, "diff": diff, "plain_sd_16x4": plain, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -62,6 +62,7 @@ struct lgf_ctx {
     int V = 0;
     int flags = 0;
     bool mixed = false, track = true;
+    bool plain = false;  // steepest descent without Fourier acceleration
     cudaStream_t stream = nullptr;   // user stream for launches
     cudaStream_t cap = nullptr;      // private stream used to capture graphs
     Lat lat{};
@@ -165,10 +166,14 @@ void launch_body(lgf_ctx* c, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, vec2_t<
 {
     vec2_t<T>* Fd = reinterpret_cast<vec2_t<T>*>(c->Fd);
     const Shape& sh = shape_of<T>(c);
-    launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl);
-    launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g, c->ctl);
+    if (c->plain) {
+        launch_build_g<T>(c->lat, s, Fd, g, c->ctl);
+    } else {
+        launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl);
+        launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g, c->ctl);
+    }
     launch_update<T>(c->lat, s, U, G, g, c->ctl, ah_of<T>(c), fs_of<T>(c));
-    launch_delta<T>(c->lat, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl, c->hist, true);
+    launch_delta<T>(c->lat, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl, c->hist, !c->plain);
 }
 
 // ---------------------------------------------------------------- graph
@@ -234,21 +239,21 @@ int append_fix(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps
         launch_mixed_prep(c->cap, c->V, c->U64, c->U32, c->G32, c->ctl);
         launch_ah_init<float>(c->lat, c->cap, c->U32, c->AH32, c->Fs32);
         launch_delta<float>(c->lat, c->sh32, c->tb, c->cap, c->AH32, c->Fs32, reinterpret_cast<float2*>(c->Fd),
-                            c->partials, c->ctl, c->hist, true);
+                            c->partials, c->ctl, c->hist, !c->plain);
         CKR(capture_end(c, deps));
         CKR(add_loop<float>(c, graph, deps, c->U32, c->G32, c->g32));
         CKR(capture_begin(c, graph, deps));
         launch_switch(c->cap, c->lat, c->G32, c->g64, c->U64, c->G64, c->ctl);
         launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
         launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
-                             true);
+                             !c->plain);
         CKR(capture_end(c, deps));
         CKR(add_loop<double>(c, graph, deps, c->U64, c->G64, c->g64));
     } else {
         CKR(capture_begin(c, graph, deps));
         launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
         launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
-                             true);
+                             !c->plain);
         CKR(capture_end(c, deps));
         CKR(add_loop<double>(c, graph, deps, c->U64, c->track ? c->G64 : nullptr, c->g64));
     }
@@ -363,6 +368,7 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     c->V = (int)V;
     c->flags = flags;
     c->mixed = (flags & LGF_MIXED) != 0;
+    c->plain = (flags & LGF_PLAIN_SD) != 0;
     c->track = c->mixed || !(flags & LGF_NO_GAUGE);
     Lat& d = c->lat;
     int st = 1;
@@ -709,7 +715,7 @@ int lgf_create(const int dims[4], int flags, lgf_ctx** out)
 {
     if (!dims || !out) return LGF_ERR_ARG;
     *out = nullptr;
-    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE)) return LGF_ERR_ARG;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD)) return LGF_ERR_ARG;
     lgf_ctx* c = new (std::nothrow) lgf_ctx();
     if (!c) return LGF_ERR_ARG;
     int r = create_impl(dims, flags, c);
@@ -981,7 +987,7 @@ int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out)
 {
     if (n < 1 || !dims || !out) return LGF_ERR_ARG;
     *out = nullptr;
-    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE)) return LGF_ERR_ARG;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD)) return LGF_ERR_ARG;
     lgf_batch* b = new (std::nothrow) lgf_batch();
     if (!b) return LGF_ERR_ARG;
     int r = LGF_OK;

@@ -362,6 +362,35 @@ __global__ void __launch_bounds__(kMaxThreads) k_xyinv_g(Lat d, const XyFft F, c
     }
 }
 
+// g(x) = reunit(1 + alpha/2 D(x)) from the four packed spatial fields D (plain
+// steepest descent: the step uses Delta itself), one thread per site
+template <typename T, typename TG>
+__global__ void __launch_bounds__(256) k_build_g(Lat d, const vec2_t<T>* __restrict__ Fd, vec2_t<TG>* __restrict__ g,
+                                                 const Ctl* ctl)
+{
+    if (ld_flag(&ctl->phase_done)) return;
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    const double h = 0.5 * ctl->alpha;
+    const vec2_t<T> f0 = Fd[s], f1 = Fd[(size_t)V + s], f2 = Fd[(size_t)2 * V + s], f3 = Fd[(size_t)3 * V + s];
+    cx<double> X[6];
+    X[0] = mk<double>(1.0, h * (double)f3.x);
+    X[1] = mk<double>(h * (double)f0.x, h * (double)f0.y);
+    X[2] = mk<double>(h * (double)f1.x, h * (double)f1.y);
+    X[3] = mk<double>(-h * (double)f0.x, h * (double)f0.y);
+    X[4] = mk<double>(1.0, h * (double)f3.y);
+    X[5] = mk<double>(h * (double)f2.x, h * (double)f2.y);
+    cx<double> gm[6];
+    gram_schmidt01(X, gm);
+    cx<TG> gs[9];
+#pragma unroll
+    for (int e = 0; e < 6; e++) gs[e] = mk<TG>((TG)gm[e].re, (TG)gm[e].im);
+    complete_row2(gs, gs + 6);
+#pragma unroll
+    for (int e = 0; e < 9; e++) st<TG>(g + (size_t)e * V + s, gs[e]);
+}
+
 // ---------------------------------------------------------------- k_update
 
 // One thread per site.  G may be null (gauge not tracked).  Also writes the

@@ -85,6 +85,11 @@ void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_
                                                                    tw_of<T>(tb, 1));
 }
 
+template <typename T> void launch_build_g(const Lat& d, cudaStream_t s, const vec2_t<T>* Fd, vec2_t<T>* g, const Ctl* ctl)
+{
+    k_build_g<T, T><<<(d.V + 255) / 256, 256, 0, s>>>(d, Fd, g, ctl);
+}
+
 template <typename T>
 void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, bool inv)
 {
@@ -110,6 +115,7 @@ void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, con
     template void launch_zt<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, vec2_t<T>*, const Ctl*);    \
     template void launch_xyinv_g<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, const vec2_t<T>*,     \
                                     vec2_t<T>*, const Ctl*);                                                      \
+    template void launch_build_g<T>(const Lat&, cudaStream_t, const vec2_t<T>*, vec2_t<T>*, const Ctl*);          \
     template void launch_xy_fft<T>(const Lat&, const Shape&, const Tables&, cudaStream_t, vec2_t<T>*, bool);      \
     template void launch_update<T>(const Lat&, cudaStream_t, vec2_t<T>*, vec2_t<T>*, const vec2_t<T>*, Ctl*,       \
                                    vec2_t<T>*, T*);

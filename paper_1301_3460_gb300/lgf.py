@@ -32,6 +32,7 @@ LGF_ERR_STATE = 8
 LGF_FP64 = 0
 LGF_MIXED = 1
 LGF_NO_GAUGE = 2
+LGF_PLAIN_SD = 4
 
 _lock = threading.Lock()
 _lib = None
@@ -144,11 +145,13 @@ def _out(like, shape, device):
 class Lattice:
     """One gauge field on the GPU and its gauge-fixing state (an lgf_ctx)."""
 
-    def __init__(self, dims, mixed: bool = False, track_gauge: bool = True, stream=None):
+    def __init__(self, dims, mixed: bool = False, track_gauge: bool = True, stream=None, accelerate: bool = True):
         lib = load()
         self.dims = tuple(int(v) for v in dims)
         self.V = int(np.prod(self.dims))
         flags = (LGF_MIXED if mixed else LGF_FP64) | (0 if track_gauge else LGF_NO_GAUGE)
+        if not accelerate:
+            flags |= LGF_PLAIN_SD
         arr = (ctypes.c_int * 4)(*self.dims)
         h = ctypes.c_void_p()
         _check(lib.lgf_create(arr, flags, ctypes.byref(h)), "lgf_create")
