@@ -429,10 +429,27 @@ void free_all(lgf_ctx* c)
 }
 
 // copy a caller array to device memory (or use it in place) and return the device pointer
+// Device address of a page-locked (pinned or registered) host buffer, so that a
+// kernel can read or write it in place over the host link; null for pageable
+// memory.
+const void* mapped_host(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 int stage_in(lgf_ctx* c, const double* p, size_t bytes, int on_device, const double** out)
 {
     if (on_device) {
         *out = p;
+        return LGF_OK;
+    }
+    if (const void* d = mapped_host(p)) {  // pinned host memory: the kernel reads it directly
+        *out = static_cast<const double*>(d);
         return LGF_OK;
     }
     CKR(ensure_stage(c, bytes));
@@ -441,20 +458,26 @@ int stage_in(lgf_ctx* c, const double* p, size_t bytes, int on_device, const dou
     return LGF_OK;
 }
 
-int stage_out_begin(lgf_ctx* c, double* p, size_t bytes, int on_device, double** dev)
+// *dev: where the kernel writes; *copy: whether stage_out_end must copy it to p.
+// Host outputs always go through the device staging buffer and one copy: a
+// kernel's scattered 144-byte records written straight into pinned host memory
+// cross the host link seven times slower than one bulk copy.
+int stage_out_begin(lgf_ctx* c, double* p, size_t bytes, int on_device, double** dev, bool* copy)
 {
+    *copy = false;
     if (on_device) {
         *dev = p;
         return LGF_OK;
     }
     CKR(ensure_stage(c, bytes));
     *dev = c->stage;
+    *copy = true;
     return LGF_OK;
 }
 
-int stage_out_end(lgf_ctx* c, double* p, size_t bytes, int on_device)
+int stage_out_end(lgf_ctx* c, double* p, size_t bytes, bool copy)
 {
-    if (!on_device) CK(cudaMemcpyAsync(p, c->stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (copy) CK(cudaMemcpyAsync(p, c->stage, bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaGetLastError());
     return LGF_OK;
@@ -807,10 +830,11 @@ int lgf_get_links(lgf_ctx* c, double* U_out, int on_device)
     if (!c->have_links) return LGF_ERR_STATE;
     const size_t bytes = (size_t)4 * c->V * 18 * sizeof(double);
     double* dst;
-    CKR(stage_out_begin(c, U_out, bytes, on_device, &dst));
+    bool copy;
+    CKR(stage_out_begin(c, U_out, bytes, on_device, &dst, &copy));
     launch_unpack_su3_64(c->stream, c->V, 4, c->U64, dst);
     CK(cudaGetLastError());
-    return stage_out_end(c, U_out, bytes, on_device);
+    return stage_out_end(c, U_out, bytes, copy);
 }
 
 int lgf_get_gauge(lgf_ctx* c, double* G_out, int on_device)
@@ -820,10 +844,11 @@ int lgf_get_gauge(lgf_ctx* c, double* G_out, int on_device)
     if (!c->have_links) return LGF_ERR_STATE;
     const size_t bytes = (size_t)c->V * 18 * sizeof(double);
     double* dst;
-    CKR(stage_out_begin(c, G_out, bytes, on_device, &dst));
+    bool copy;
+    CKR(stage_out_begin(c, G_out, bytes, on_device, &dst, &copy));
     launch_unpack_su3_64(c->stream, c->V, 1, c->G64, dst);
     CK(cudaGetLastError());
-    return stage_out_end(c, G_out, bytes, on_device);
+    return stage_out_end(c, G_out, bytes, copy);
 }
 
 int lgf_get_history(lgf_ctx* c, double* theta_F, int n_max, int* written)
@@ -860,10 +885,11 @@ int lgf_delta(lgf_ctx* c, double* Delta_out, int on_device, double* theta, doubl
     if (Delta_out) {
         const size_t bytes = (size_t)c->V * 18 * sizeof(double);
         double* dst;
-        CKR(stage_out_begin(c, Delta_out, bytes, on_device, &dst));
+        bool copy;
+        CKR(stage_out_begin(c, Delta_out, bytes, on_device, &dst, &copy));
         launch_unpack_delta(c->stream, c->V, Fd, dst);
         CK(cudaGetLastError());
-        CKR(stage_out_end(c, Delta_out, bytes, on_device));
+        CKR(stage_out_end(c, Delta_out, bytes, copy));
     }
     CK(cudaMemcpyAsync(c->host_ctl, c->ctl_stage, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -886,10 +912,11 @@ int lgf_accelerate(lgf_ctx* c, const double* Delta_in, double* Dt_out, int on_de
     launch_xy_fft<double>(c->lat, c->sh64, c->tb, c->stream, Fd, true);
     CK(cudaGetLastError());
     double* dst;
-    CKR(stage_out_begin(c, Dt_out, bytes, on_device, &dst));
+    bool copy;
+    CKR(stage_out_begin(c, Dt_out, bytes, on_device, &dst, &copy));
     launch_unpack_delta(c->stream, c->V, Fd, dst);
     CK(cudaGetLastError());
-    return stage_out_end(c, Dt_out, bytes, on_device);
+    return stage_out_end(c, Dt_out, bytes, copy);
 }
 
 int lgf_build_g(lgf_ctx* c, const double* Dt_in, double alpha, double* g_out, int on_device)
@@ -909,10 +936,11 @@ int lgf_build_g(lgf_ctx* c, const double* Dt_in, double alpha, double* g_out, in
     launch_xyinv_g<double>(c->lat, c->sh64, c->tb, c->stream, Fd, c->g64, c->ctl_stage);
     CK(cudaGetLastError());
     double* dst;
-    CKR(stage_out_begin(c, g_out, bytes, on_device, &dst));
+    bool copy;
+    CKR(stage_out_begin(c, g_out, bytes, on_device, &dst, &copy));
     launch_unpack_full(c->stream, c->V, c->g64, dst);
     CK(cudaGetLastError());
-    return stage_out_end(c, g_out, bytes, on_device);
+    return stage_out_end(c, g_out, bytes, copy);
 }
 
 int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double* ms)
@@ -1038,6 +1066,7 @@ int lgf_batch_set_links(lgf_batch* b, int i, const double* U, int on_device)
     if (!b || !U || i < 0 || i >= (int)b->ctx.size()) return LGF_ERR_ARG;
     lgf_ctx* c = b->ctx[i];
     if (on_device) return lgf_set_links(c, U, 1);
+    if (mapped_host(U)) return lgf_set_links(c, U, 0);  // pinned: read in place
     // host arrays go through one staging buffer shared by the whole batch
     const size_t bytes = (size_t)4 * c->V * 18 * sizeof(double);
     if (b->stage_bytes < bytes) {
