@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-links18", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble")
     return ap.parse_args()
@@ -308,6 +309,31 @@ def run_ours(args, dims):
                                      "gflops": per32[k]["flops"] * V / msm[k] / 1e6} for k in msm}
         latm.close()
 
+    # link parametrisation: the same FP64 workload with row 2 kept in memory (18 reals)
+    links18 = None
+    if not args.no_links18:
+        l18 = lgf.Lattice(dims, links18=True, stream=stream)
+        l18.set_links(dev[1])
+        l18.autotune()
+        for k in range(1):
+            l18.set_links(dev[k % len(dev)])
+            l18.fix(args.alpha, args.tol, args.max_iter)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n18 = 0
+        e0.record(stream)
+        for k in range(args.steps):
+            l18.set_links(dev[k % len(dev)])
+            n18 += l18.fix(args.alpha, args.tol, args.max_iter)["iters"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        T18 = e0.elapsed_time(e1) / 1000.0
+        l18.set_links(dev[1])
+        ms18 = l18.time_kernels(args.alpha, n_iter=8, precision=64)
+        l18.close()
+        links18 = {"value": n18 / T18, "unit": "iters/s", "ms_per_step": 1000 * T18 / args.steps,
+                   "update_ms": ms18["update"], "kernels_ms": ms18}
+
     # critical slowing down: plain steepest descent against the accelerated method at 16^4
     plain = None
     if not args.no_plain:
@@ -406,7 +432,8 @@ def run_ours(args, dims):
             "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol,
                        "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
                        % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
-            "time_to_theta": ttt, "mixed": mixed, "diff": diff, "plain_sd_16x4": plain, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "time_to_theta": ttt, "mixed": mixed, "links18": links18, "diff": diff, "plain_sd_16x4": plain,
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -58,6 +58,9 @@ typedef enum {
 #define LGF_FP64 0        /* every step in FP64 */
 #define LGF_MIXED 1       /* FP32 Delta/FFT/update until theta < switch_tol, then FP64 (see lgf_set_switch_tol) */
 #define LGF_NO_GAUGE 2    /* do not accumulate G (lgf_get_gauge then fails); FP64 mode only */
+#define LGF_LINKS18 8     /* keep row 2 of each FP64 link in memory (18 reals) instead of rebuilding it on
+                             every load (12 reals): the same values (row 2 is stored as the rebuild from
+                             rows 0,1), 50% more link bytes, fewer FP64 operations per update */
 #define LGF_PLAIN_SD 4    /* steepest descent without Fourier acceleration: g = reunit(1 + alpha/2 Delta);
                              the method whose critical slowing down the introduction cites (alpha < 0.125
                              for stability with this Delta normalisation) */
@@ -67,7 +70,8 @@ typedef enum {
  * Each extent must be one of 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128 and the
  * plane sizes must satisfy Lx*Ly <= 3072 and Lz*Lt <= 12288 (the FFT tiles are
  * held in shared memory); else LGF_ERR_UNSUPPORTED_DIMS.  flags: LGF_FP64 or
- * LGF_MIXED, optionally | LGF_NO_GAUGE, | LGF_PLAIN_SD.  *out receives the context.
+ * LGF_MIXED, optionally | LGF_NO_GAUGE, | LGF_PLAIN_SD, | LGF_LINKS18.  *out receives the
+ * context.
  */
 int lgf_create(const int dims[4], int flags, lgf_ctx** out);
 

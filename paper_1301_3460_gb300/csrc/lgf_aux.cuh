@@ -25,7 +25,7 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double 
 // Interleaved [4][V][3][3] complex128 -> rows 0,1 planes of T; optional SU(3)
 // check of the full input matrix: err[0] = max |U U^dag - 1|, err[1] = max |det U - 1|.
 template <typename T>
-static __global__ void k_pack_links(int V, const double* __restrict__ in, vec2_t<T>* __restrict__ U,
+static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in, vec2_t<T>* __restrict__ U,
                              unsigned long long* err, int validate)
 {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;  // link index mu*V + s
@@ -41,7 +41,16 @@ static __global__ void k_pack_links(int V, const double* __restrict__ in, vec2_t
             vec2_t<T> v;
             v.x = (T)m[e].re;
             v.y = (T)m[e].im;
-            U[(size_t)(mu * 6 + e) * V + s] = v;
+            U[(size_t)(mu * ne + e) * V + s] = v;
+        }
+        if (ne == 9) {
+            // row 2 stored as the rebuild from rows 0,1, as a 12-real load would give it
+            cx<T> r[9];
+#pragma unroll
+            for (int e = 0; e < 6; e++) r[e] = mk<T>((T)m[e].re, (T)m[e].im);
+            complete_row2(r, r + 6);
+#pragma unroll
+            for (int e = 6; e < 9; e++) st<T>(U + (size_t)(mu * 9 + e) * V + s, r[e]);
         }
         if (validate) {
 #pragma unroll
@@ -77,17 +86,15 @@ static __global__ void k_pack_links(int V, const double* __restrict__ in, vec2_t
     }
 }
 
-// rows 0,1 planes -> interleaved [nmat][V][3][3] complex128 with row 2 rebuilt
+// [nmat][ne][V] planes -> interleaved [nmat][V][3][3] complex128 (row 2 rebuilt or read)
 template <typename T>
-static __global__ void k_unpack_su3(int V, int nmat, const vec2_t<T>* __restrict__ U, double* __restrict__ out)
+static __global__ void k_unpack_su3(int V, int nmat, int ne, const vec2_t<T>* __restrict__ U, double* __restrict__ out)
 {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)nmat * V) return;
     const int mu = (int)(idx / V), s = (int)(idx - (long)mu * V);
     cx<T> m[9];
-#pragma unroll
-    for (int e = 0; e < 6; e++) m[e] = ld<T>(U + (size_t)(mu * 6 + e) * V + s);
-    complete_row2(m, m + 6);
+    load_link<T>(U, V, ne, mu, s, m);
     double* p = out + idx * 18;
 #pragma unroll
     for (int e = 0; e < 9; e++) {
@@ -171,18 +178,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_fft(Lat d, const XyFft F, ve
 
 // ---------------------------------------------------------------- mixed mode
 
-// start of the FP32 phase: FP32 copy of the current FP64 links, G32 = 1
-static __global__ void k_mixed_prep(int V, const double2* __restrict__ U64, float2* __restrict__ U32,
+// start of the FP32 phase: FP32 copy (rows 0,1) of the current FP64 links
+// (layout [mu][ne][V]), G32 = 1
+static __global__ void k_mixed_prep(int V, int ne, const double2* __restrict__ U64, float2* __restrict__ U32,
                              float2* __restrict__ G32, const Ctl* ctl)
 {
     if (ld_flag(&ctl->done)) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
 #pragma unroll
-    for (int e = 0; e < 24; e++) {
-        const double2 v = U64[(size_t)e * V + s];
-        U32[(size_t)e * V + s] = make_float2((float)v.x, (float)v.y);
-    }
+    for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+        for (int e = 0; e < 6; e++) {
+            const double2 v = U64[(size_t)(mu * ne + e) * V + s];
+            U32[(size_t)(mu * 6 + e) * V + s] = make_float2((float)v.x, (float)v.y);
+        }
 #pragma unroll
     for (int e = 0; e < 6; e++) G32[(size_t)e * V + s] = make_float2((e == 0 || e == 4) ? 1.f : 0.f, 0.f);
 }
@@ -221,7 +231,7 @@ static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restri
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         cx<double> u[9];
-        load_link<double>(U, V, mu, s, u);
+        load_link<double>(U, V, d.ne, mu, s, u);
         cx<double> A[6];
 #pragma unroll
         for (int i = 0; i < 2; i++)
@@ -234,6 +244,7 @@ static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restri
             }
         cx<double> gn[9];
         load_g<double>(Gs, V, site_shift(d, s, c[mu], mu, +1), gn);
+        cx<double> w[9];
 #pragma unroll
         for (int i = 0; i < 2; i++)
 #pragma unroll
@@ -241,8 +252,14 @@ static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restri
                 cx<double> acc = cmulc(A[3 * i], gn[3 * j]);
                 acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
                 acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
-                st<double>(U + (size_t)(mu * 6 + 3 * i + j) * V + s, acc);
+                w[3 * i + j] = acc;
+                st<double>(U + (size_t)(mu * d.ne + 3 * i + j) * V + s, acc);
             }
+        if (d.ne == 9) {
+            complete_row2(w, w + 6);
+#pragma unroll
+            for (int e = 6; e < 9; e++) st<double>(U + (size_t)(mu * 9 + e) * V + s, w[e]);
+        }
     }
     if (G != nullptr) {
         cx<double> Gm[9];

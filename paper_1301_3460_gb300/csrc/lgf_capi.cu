@@ -65,7 +65,8 @@ struct lgf_ctx {
     bool plain = false;  // steepest descent without Fourier acceleration
     cudaStream_t stream = nullptr;   // user stream for launches
     cudaStream_t cap = nullptr;      // private stream used to capture graphs
-    Lat lat{};
+    Lat lat{};    // FP64 kernels (links with ne = 6 or 9 entries)
+    Lat lat32{};  // FP32 kernels (always 6: rows 0,1)
     Shape sh64{}, sh32{};
     Tables tb{};
     // state
@@ -156,6 +157,10 @@ template <typename T> T* fs_of(lgf_ctx* c);
 template <> double* fs_of<double>(lgf_ctx* c) { return c->Fs64; }
 template <> float* fs_of<float>(lgf_ctx* c) { return c->Fs32; }
 
+template <typename T> const Lat& lat_of(const lgf_ctx* c);
+template <> const Lat& lat_of<double>(const lgf_ctx* c) { return c->lat; }
+template <> const Lat& lat_of<float>(const lgf_ctx* c) { return c->lat32; }
+
 template <typename T> const Shape& shape_of(const lgf_ctx* c);
 template <> const Shape& shape_of<double>(const lgf_ctx* c) { return c->sh64; }
 template <> const Shape& shape_of<float>(const lgf_ctx* c) { return c->sh32; }
@@ -166,14 +171,15 @@ void launch_body(lgf_ctx* c, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, vec2_t<
 {
     vec2_t<T>* Fd = reinterpret_cast<vec2_t<T>*>(c->Fd);
     const Shape& sh = shape_of<T>(c);
+    const Lat& d = lat_of<T>(c);
     if (c->plain) {
-        launch_build_g<T>(c->lat, s, Fd, g, c->ctl);
+        launch_build_g<T>(d, s, Fd, g, c->ctl);
     } else {
-        launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl);
-        launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g, c->ctl);
+        launch_zt<T>(d, sh, c->tb, s, Fd, c->ctl);
+        launch_xyinv_g<T>(d, sh, c->tb, s, Fd, g, c->ctl);
     }
-    launch_update<T>(c->lat, s, U, G, g, c->ctl, ah_of<T>(c), fs_of<T>(c));
-    launch_delta<T>(c->lat, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl, c->hist, !c->plain);
+    launch_update<T>(d, s, U, G, g, c->ctl, ah_of<T>(c), fs_of<T>(c));
+    launch_delta<T>(d, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl, c->hist, !c->plain);
 }
 
 // ---------------------------------------------------------------- graph
@@ -236,9 +242,9 @@ int append_fix(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps
     double2* Fd64 = reinterpret_cast<double2*>(c->Fd);
     if (c->mixed) {
         CKR(capture_begin(c, graph, deps));
-        launch_mixed_prep(c->cap, c->V, c->U64, c->U32, c->G32, c->ctl);
-        launch_ah_init<float>(c->lat, c->cap, c->U32, c->AH32, c->Fs32);
-        launch_delta<float>(c->lat, c->sh32, c->tb, c->cap, c->AH32, c->Fs32, reinterpret_cast<float2*>(c->Fd),
+        launch_mixed_prep(c->cap, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl);
+        launch_ah_init<float>(c->lat32, c->cap, c->U32, c->AH32, c->Fs32);
+        launch_delta<float>(c->lat32, c->sh32, c->tb, c->cap, c->AH32, c->Fs32, reinterpret_cast<float2*>(c->Fd),
                             c->partials, c->ctl, c->hist, !c->plain);
         CKR(capture_end(c, deps));
         CKR(add_loop<float>(c, graph, deps, c->U32, c->G32, c->g32));
@@ -380,6 +386,9 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     d.V = c->V;
     d.P = dims[0] * dims[1];
     d.nplanes = dims[2] * dims[3];
+    d.ne = (flags & LGF_LINKS18) ? 9 : 6;
+    c->lat32 = d;
+    c->lat32.ne = 6;
     if (!pick_shape(d, sizeof(double2), 2, 4, &c->sh64)) return LGF_ERR_UNSUPPORTED_DIMS;
     if (!pick_shape(d, sizeof(float2), 2, 8, &c->sh32)) return LGF_ERR_UNSUPPORTED_DIMS;
 
@@ -391,7 +400,7 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     if (c->mixed) CK(prepare_kernels<float>(d, c->sh32));
 
     const size_t Vs = (size_t)c->V;
-    CKR(alloc((void**)&c->U64, 24 * Vs * sizeof(double2)));
+    CKR(alloc((void**)&c->U64, (size_t)4 * d.ne * Vs * sizeof(double2)));
     if (c->track) CKR(alloc((void**)&c->G64, 6 * Vs * sizeof(double2)));
     CKR(alloc((void**)&c->g64, 9 * Vs * sizeof(double2)));
     CKR(alloc(&c->Fd, 4 * Vs * sizeof(double2)));
@@ -525,11 +534,11 @@ template <typename T> int time_shape(lgf_ctx* c, const Shape& sh, int which, flo
     for (int r = 0; r <= reps; r++) {
         if (r == 1) cudaEventRecord(e0, s);
         if (which == 0) {
-            launch_delta<T>(c->lat, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl_stage, nullptr,
-                            true);
-            launch_xyinv_g<T>(c->lat, sh, c->tb, s, Fd, g_of<T>(c), c->ctl_stage);
+            launch_delta<T>(lat_of<T>(c), sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl_stage,
+                            nullptr, true);
+            launch_xyinv_g<T>(lat_of<T>(c), sh, c->tb, s, Fd, g_of<T>(c), c->ctl_stage);
         } else {
-            launch_zt<T>(c->lat, sh, c->tb, s, Fd, c->ctl_stage);
+            launch_zt<T>(lat_of<T>(c), sh, c->tb, s, Fd, c->ctl_stage);
         }
     }
     cudaEventRecord(e1, s);
@@ -565,7 +574,7 @@ template <typename T> int autotune_prec(lgf_ctx* c)
     for (int nt : nts)
         for (int nfc = 1; nfc <= 4; nfc <<= 1) {
             Shape cand;
-            if (!make_shape(c->lat, elem, nt, nfc, best.nt_zt, best.zt.xw, &cand)) continue;
+            if (!make_shape(lat_of<T>(c), elem, nt, nfc, best.nt_zt, best.zt.xw, &cand)) continue;
             float ms;
             CKR(time_shape<T>(c, cand, 0, &ms));
             if (ms < best_xy) {
@@ -577,7 +586,7 @@ template <typename T> int autotune_prec(lgf_ctx* c)
     for (int nt : nts)
         for (int xw = 1; xw <= 16; xw <<= 1) {
             Shape cand;
-            if (!make_shape(c->lat, elem, best.nt_xy, best.xy.nfc, nt, xw, &cand)) continue;
+            if (!make_shape(lat_of<T>(c), elem, best.nt_xy, best.xy.nfc, nt, xw, &cand)) continue;
             float ms;
             CKR(time_shape<T>(c, cand, 1, &ms));
             if (ms < best_zt) {
@@ -599,8 +608,8 @@ int autotune_ctx(lgf_ctx* c)
     launch_ah_init<double>(c->lat, c->stream, c->U64, c->AH64, c->Fs64);
     CKR(autotune_prec<double>(c));
     if (c->mixed) {
-        launch_mixed_prep(c->stream, c->V, c->U64, c->U32, c->G32, c->ctl_stage);
-        launch_ah_init<float>(c->lat, c->stream, c->U32, c->AH32, c->Fs32);
+        launch_mixed_prep(c->stream, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl_stage);
+        launch_ah_init<float>(c->lat32, c->stream, c->U32, c->AH32, c->Fs32);
         CKR(autotune_prec<float>(c));
     }
     CK(cudaStreamSynchronize(c->stream));
@@ -738,7 +747,7 @@ int lgf_create(const int dims[4], int flags, lgf_ctx** out)
 {
     if (!dims || !out) return LGF_ERR_ARG;
     *out = nullptr;
-    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD)) return LGF_ERR_ARG;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD | LGF_LINKS18)) return LGF_ERR_ARG;
     lgf_ctx* c = new (std::nothrow) lgf_ctx();
     if (!c) return LGF_ERR_ARG;
     int r = create_impl(dims, flags, c);
@@ -788,7 +797,7 @@ int lgf_set_links(lgf_ctx* c, const double* U, int on_device)
     c->have_links = false;
     CKR(stage_in(c, U, bytes, on_device, &src));
     CK(cudaMemsetAsync(c->err, 0, 2 * sizeof(unsigned long long), c->stream));
-    launch_pack_links64(c->stream, c->V, src, c->U64, c->err);
+    launch_pack_links64(c->stream, c->V, c->lat.ne, src, c->U64, c->err);
     if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
     CK(cudaGetLastError());
     unsigned long long e[2];
@@ -832,7 +841,7 @@ int lgf_get_links(lgf_ctx* c, double* U_out, int on_device)
     double* dst;
     bool copy;
     CKR(stage_out_begin(c, U_out, bytes, on_device, &dst, &copy));
-    launch_unpack_su3_64(c->stream, c->V, 4, c->U64, dst);
+    launch_unpack_su3_64(c->stream, c->V, 4, c->lat.ne, c->U64, dst);
     CK(cudaGetLastError());
     return stage_out_end(c, U_out, bytes, copy);
 }
@@ -846,7 +855,7 @@ int lgf_get_gauge(lgf_ctx* c, double* G_out, int on_device)
     double* dst;
     bool copy;
     CKR(stage_out_begin(c, G_out, bytes, on_device, &dst, &copy));
-    launch_unpack_su3_64(c->stream, c->V, 1, c->G64, dst);
+    launch_unpack_su3_64(c->stream, c->V, 1, 6, c->G64, dst);
     CK(cudaGetLastError());
     return stage_out_end(c, G_out, bytes, copy);
 }
@@ -956,8 +965,8 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
     cudaStream_t s = c->stream;
     int rc = LGF_OK;
     if (precision == 32) {
-        launch_mixed_prep(s, c->V, c->U64, c->U32, c->G32, c->ctl_stage);
-        launch_ah_init<float>(c->lat, s, c->U32, c->AH32, c->Fs32);
+        launch_mixed_prep(s, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl_stage);
+        launch_ah_init<float>(c->lat32, s, c->U32, c->AH32, c->Fs32);
     } else {
         launch_ah_init<double>(c->lat, s, c->U64, c->AH64, c->Fs64);
     }
@@ -976,14 +985,14 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
                                   c->Fs64);
         } else {
             float2* Fd = reinterpret_cast<float2*>(c->Fd);
-            launch_delta<float>(c->lat, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, c->ctl_stage, nullptr,
+            launch_delta<float>(c->lat32, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, c->ctl_stage, nullptr,
                                 true);
             cudaEventRecord(ev[1], s);
-            launch_zt<float>(c->lat, c->sh32, c->tb, s, Fd, c->ctl_stage);
+            launch_zt<float>(c->lat32, c->sh32, c->tb, s, Fd, c->ctl_stage);
             cudaEventRecord(ev[2], s);
-            launch_xyinv_g<float>(c->lat, c->sh32, c->tb, s, Fd, c->g32, c->ctl_stage);
+            launch_xyinv_g<float>(c->lat32, c->sh32, c->tb, s, Fd, c->g32, c->ctl_stage);
             cudaEventRecord(ev[3], s);
-            launch_update<float>(c->lat, s, c->U32, c->G32, c->g32, c->ctl_stage, c->AH32, c->Fs32);
+            launch_update<float>(c->lat32, s, c->U32, c->G32, c->g32, c->ctl_stage, c->AH32, c->Fs32);
         }
         cudaEventRecord(ev[4], s);
         cudaError_t e = cudaEventSynchronize(ev[4]);
@@ -1015,7 +1024,7 @@ int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out)
 {
     if (n < 1 || !dims || !out) return LGF_ERR_ARG;
     *out = nullptr;
-    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD)) return LGF_ERR_ARG;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD | LGF_LINKS18)) return LGF_ERR_ARG;
     lgf_batch* b = new (std::nothrow) lgf_batch();
     if (!b) return LGF_ERR_ARG;
     int r = LGF_OK;

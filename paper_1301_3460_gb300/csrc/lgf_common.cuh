@@ -113,6 +113,8 @@ struct Lat {
     int V;
     int P;         // Lx*Ly
     int nplanes;   // Lz*Lt
+    int ne;        // complex entries stored per link: 6 (rows 0,1; row 2 rebuilt on load)
+                   // or 9 (row 2 kept as written, the rebuild done once when stored)
 };
 
 __device__ __forceinline__ int site_shift(const Lat& d, int s, int c_mu, int mu, int dir)

@@ -140,7 +140,7 @@ static __global__ void __launch_bounds__(128) k_bwd_update(Lat d, const double2*
 #pragma unroll 1
     for (int mu = 0; mu < 4; mu++) {
         C u[9];
-        load_link<double>(U, V, mu, s, u);
+        load_link<double>(U, V, d.ne, mu, s, u);
         C gn[9];
         load9(g, V, site_shift(d, s, c[mu], mu, +1), gn);
         // Vr = rows 0,1 of g(x) U; Up = Vr gn^dag
@@ -331,7 +331,7 @@ static __global__ void k_bwd_delta(Lat d, const double2* __restrict__ U, const d
 #pragma unroll
         for (int e = 0; e < 9; e++) Gu[e] = Gu[e] + GMn[e] - GMx[e];
         C u[9];
-        load_link<double>(U, V, mu, s, u);
+        load_link<double>(U, V, d.ne, mu, s, u);
         row2_bwd(u, u + 3, Gu + 6, Gu, Gu + 3);
         Gu[6] = Gu[7] = Gu[8] = mk<double>(0, 0);
         store9(Gin + (size_t)mu * 9 * V, V, s, Gu);
@@ -360,7 +360,7 @@ static __global__ void __launch_bounds__(256) k_gluon_partial(Lat d, const doubl
         int c[4];
         site_coords(d, s, c);
         C u[9];
-        load_link<double>(U, V, mu, s, u);
+        load_link<double>(U, V, d.ne, mu, s, u);
         C A[9];
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -471,7 +471,7 @@ static __global__ void k_gluon_bwd(Lat d, const double2* __restrict__ U, const d
 #pragma unroll
             for (int j = 0; j < 3; j++) Gu[3 * i + j] = ihalf(GA[3 * i + j] + conjg(GA[3 * j + i]));
         C u[9];
-        load_link<double>(U, V, mu, s, u);
+        load_link<double>(U, V, d.ne, mu, s, u);
         row2_bwd(u, u + 3, Gu + 6, Gu, Gu + 3);
         Gu[6] = Gu[7] = Gu[8] = mk<double>(0, 0);
         store9(Gout + (size_t)mu * 9 * V, V, s, Gu);

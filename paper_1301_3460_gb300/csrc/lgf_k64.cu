@@ -11,13 +11,13 @@ namespace {
 inline unsigned blocks(long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 }  // namespace
 
-void launch_pack_links64(cudaStream_t s, int V, const double* in, double2* U, unsigned long long* err)
+void launch_pack_links64(cudaStream_t s, int V, int ne, const double* in, double2* U, unsigned long long* err)
 {
-    k_pack_links<double><<<blocks(4L * V, 256), 256, 0, s>>>(V, in, U, err, 1);
+    k_pack_links<double><<<blocks(4L * V, 256), 256, 0, s>>>(V, ne, in, U, err, 1);
 }
-void launch_unpack_su3_64(cudaStream_t s, int V, int nmat, const double2* U, double* out)
+void launch_unpack_su3_64(cudaStream_t s, int V, int nmat, int ne, const double2* U, double* out)
 {
-    k_unpack_su3<double><<<blocks((long)nmat * V, 256), 256, 0, s>>>(V, nmat, U, out);
+    k_unpack_su3<double><<<blocks((long)nmat * V, 256), 256, 0, s>>>(V, nmat, ne, U, out);
 }
 void launch_identity_rows64(cudaStream_t s, int V, double2* G)
 {
@@ -35,9 +35,9 @@ void launch_unpack_full(cudaStream_t s, int V, const double2* g, double* out)
 {
     k_unpack_full<<<blocks(V, 256), 256, 0, s>>>(V, g, out);
 }
-void launch_mixed_prep(cudaStream_t s, int V, const double2* U64, float2* U32, float2* G32, const Ctl* ctl)
+void launch_mixed_prep(cudaStream_t s, int V, int ne, const double2* U64, float2* U32, float2* G32, const Ctl* ctl)
 {
-    k_mixed_prep<<<blocks(V, 256), 256, 0, s>>>(V, U64, U32, G32, ctl);
+    k_mixed_prep<<<blocks(V, 256), 256, 0, s>>>(V, ne, U64, U32, G32, ctl);
 }
 void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
                    Ctl* ctl)

@@ -102,13 +102,19 @@ static __device__ void reduce_theta_F(double th, double f, double* __restrict__ 
 
 // ---------------------------------------------------------------- link loads
 
-// rows 0,1 of link (mu, s) and the rebuilt row 2
+// link (mu, s), layout [mu][ne][V]: rows 0,1 and row 2 (rebuilt as conj(r0 x r1)
+// when ne = 6, read when ne = 9, in which case it was stored as that rebuild)
 template <typename T>
-__device__ __forceinline__ void load_link(const vec2_t<T>* __restrict__ U, int V, int mu, int s, cx<T>* u)
+__device__ __forceinline__ void load_link(const vec2_t<T>* __restrict__ U, int V, int ne, int mu, int s, cx<T>* u)
 {
 #pragma unroll
-    for (int e = 0; e < 6; e++) u[e] = ld<T>(U + (size_t)(mu * 6 + e) * V + s);
-    complete_row2(u, u + 6);
+    for (int e = 0; e < 6; e++) u[e] = ld<T>(U + (size_t)(mu * ne + e) * V + s);
+    if (ne == 9) {
+#pragma unroll
+        for (int e = 6; e < 9; e++) u[e] = ld<T>(U + (size_t)(mu * 9 + e) * V + s);
+    } else {
+        complete_row2(u, u + 6);
+    }
 }
 
 template <typename T>
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(256) k_ah_init(Lat d, const vec2_t<T>* __restr
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         cx<T> u[9], a[4];
-        load_link<T>(U, V, mu, s, u);
+        load_link<T>(U, V, d.ne, mu, s, u);
         ah_pack(u, a);
 #pragma unroll
         for (int k = 0; k < 4; k++) st<T>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
@@ -419,7 +425,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         cx<T> u[9];
-        load_link<T>(U, V, mu, s, u);
+        load_link<T>(U, V, d.ne, mu, s, u);
         // A = rows 0,1 of g(x) U
         cx<T> A[6];
 #pragma unroll
@@ -443,9 +449,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
                 acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
                 acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
                 w[3 * i + j] = acc;
-                st<T>(U + (size_t)(mu * 6 + 3 * i + j) * V + s, acc);
+                st<T>(U + (size_t)(mu * d.ne + 3 * i + j) * V + s, acc);
             }
         complete_row2(w, w + 6);
+        if (d.ne == 9) {
+#pragma unroll
+            for (int e = 6; e < 9; e++) st<T>(U + (size_t)(mu * 9 + e) * V + s, w[e]);
+        }
         cx<T> a[4];
         ah_pack(w, a);
 #pragma unroll

@@ -46,13 +46,13 @@ void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, con
                    vec2_t<T>* AH, T* Fs);
 
 // conversion, checking and mode-switch kernels (FP64 unit)
-void launch_pack_links64(cudaStream_t s, int V, const double* in, double2* U, unsigned long long* err);
-void launch_unpack_su3_64(cudaStream_t s, int V, int nmat, const double2* U, double* out);
+void launch_pack_links64(cudaStream_t s, int V, int ne, const double* in, double2* U, unsigned long long* err);
+void launch_unpack_su3_64(cudaStream_t s, int V, int nmat, int ne, const double2* U, double* out);
 void launch_identity_rows64(cudaStream_t s, int V, double2* G);
 void launch_pack_delta(cudaStream_t s, int V, const double* in, double2* Fd);
 void launch_unpack_delta(cudaStream_t s, int V, const double2* Fd, double* out);
 void launch_unpack_full(cudaStream_t s, int V, const double2* g, double* out);
-void launch_mixed_prep(cudaStream_t s, int V, const double2* U64, float2* U32, float2* G32, const Ctl* ctl);
+void launch_mixed_prep(cudaStream_t s, int V, int ne, const double2* U64, float2* U32, float2* G32, const Ctl* ctl);
 void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
                    Ctl* ctl);
 void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h);

@@ -33,6 +33,7 @@ LGF_FP64 = 0
 LGF_MIXED = 1
 LGF_NO_GAUGE = 2
 LGF_PLAIN_SD = 4
+LGF_LINKS18 = 8
 
 _lock = threading.Lock()
 _lib = None
@@ -145,13 +146,16 @@ def _out(like, shape, device):
 class Lattice:
     """One gauge field on the GPU and its gauge-fixing state (an lgf_ctx)."""
 
-    def __init__(self, dims, mixed: bool = False, track_gauge: bool = True, stream=None, accelerate: bool = True):
+    def __init__(self, dims, mixed: bool = False, track_gauge: bool = True, stream=None, accelerate: bool = True,
+                 links18: bool = False):
         lib = load()
         self.dims = tuple(int(v) for v in dims)
         self.V = int(np.prod(self.dims))
         flags = (LGF_MIXED if mixed else LGF_FP64) | (0 if track_gauge else LGF_NO_GAUGE)
         if not accelerate:
             flags |= LGF_PLAIN_SD
+        if links18:
+            flags |= LGF_LINKS18
         arr = (ctypes.c_int * 4)(*self.dims)
         h = ctypes.c_void_p()
         _check(lib.lgf_create(arr, flags, ctypes.byref(h)), "lgf_create")
