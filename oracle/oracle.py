@@ -1,4 +1,6 @@
-"""ctypes front end of the plain FP64 CPU oracle (``lgf_oracle.c``).
+"""ctypes front end of the plain FP64 CPU oracle (``lgf_oracle.c`` for gauge
+fixing, ``lgf_wilson_oracle.c`` for the Wilson-action configurations it is
+applied to).
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke entry point and the benchmark's
 CPU-baseline leg are the only callers.  The CUDA library never imports this
@@ -23,6 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lgf_oracle.c")
+_SRC_W = os.path.join(_HERE, "lgf_wilson_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblgf_oracle.so")
 _lock = threading.Lock()
@@ -35,9 +38,10 @@ _int_p = ctypes.POINTER(ctypes.c_int)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (ISO C11, no fast-math, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(p) for p in (_SRC, _SRC_W))
+    if force or stale:
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_W, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -69,6 +73,14 @@ def _load():
             lib.orc_plaquette.restype = ctypes.c_double
             lib.orc_gluon_pmin.argtypes = [_int_p, v, _dbl_p]
             lib.orc_gluon_pmin.restype = ctypes.c_double
+            u64, u32 = ctypes.c_uint64, ctypes.c_uint32
+            lib.orc_wilson_sweep.argtypes = [_int_p, v, ctypes.c_double, u64, u32, ctypes.c_int]
+            lib.orc_wilson_plaquette.argtypes = [_int_p, v]
+            lib.orc_wilson_plaquette.restype = ctypes.c_double
+            lib.orc_wilson_link.argtypes = [_int_p, v, ctypes.c_long, ctypes.c_int, ctypes.c_double, u64, u32,
+                                             ctypes.c_int]
+            lib.orc_philox4x32.argtypes = [v, v, v]
+            lib.orc_su2_samples.argtypes = [ctypes.c_double, u64, ctypes.c_int, _dbl_p]
             lib.orc_threads.restype = ctypes.c_int
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -222,3 +234,49 @@ def gluon_pmin(L, U):
     Dp = (ctypes.c_double * 4)()
     avg = _load().orc_gluon_pmin(d, _ptr(U), Dp)
     return float(avg), np.array(list(Dp))
+
+
+def wilson_sweeps(L, U, beta, seed, sweeps, mode=0, first_sweep=0):
+    """Sweeps of the Wilson-action Monte Carlo (configurations of the kind the
+    paper fixes): SU(2)-subgroup heat bath (mode 0) or overrelaxation (mode 1) of
+    every link, mu = 0..3, even then odd sites (lgf_wilson_oracle.c).  Heat-bath
+    sweep n draws random numbers with sweep counter first_sweep + n.  Returns new
+    links (input untouched)."""
+    d, V = _dims(L)
+    U = _c(U, (4, V, 3, 3)).copy()
+    for n in range(int(sweeps)):
+        _load().orc_wilson_sweep(d, _ptr(U), float(beta), int(seed), int(first_sweep + n), int(mode))
+    return U
+
+
+def wilson_link(L, U, site, mu, beta, seed, sweep, mode=0):
+    """The update of one link U_mu(site) given all other links (as inside a
+    sweep).  Returns new links (input untouched)."""
+    d, V = _dims(L)
+    U = _c(U, (4, V, 3, 3)).copy()
+    _load().orc_wilson_link(d, _ptr(U), int(site), int(mu), float(beta), int(seed), int(sweep), int(mode))
+    return U
+
+
+def wilson_plaquette(L, U) -> float:
+    """Mean of Re Tr U_P / 3 over all plaquettes (independent loop of this file)."""
+    d, V = _dims(L)
+    U = _c(U, (4, V, 3, 3))
+    return float(_load().orc_wilson_plaquette(d, _ptr(U)))
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of a 4-word counter and 2-word key (Salmon et al., SC'11)."""
+    c = np.array(ctr, np.uint32)
+    k = np.array(key, np.uint32)
+    out = np.empty(4, np.uint32)
+    _load().orc_philox4x32(c.ctypes.data_as(ctypes.c_void_p), k.ctypes.data_as(ctypes.c_void_p),
+                           out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def su2_samples(b, seed, n):
+    """n draws y = (y0, y1, y2, y3) of the SU(2) heat-bath sampler for parameter b."""
+    y = np.empty((int(n), 4), np.float64)
+    _load().orc_su2_samples(float(b), int(seed), int(n), y.ctypes.data_as(_dbl_p))
+    return y
