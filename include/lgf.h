@@ -240,6 +240,35 @@ int lgf_gluon_pmin_bwd(lgf_ctx* ctx, double gD, double* gU);
  */
 int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in, double* Dt_out, void* cuda_stream);
 
+/*
+ * Configurations to fix, made on the device (the paper fixes Wilson-action
+ * configurations and does not say how it made them).  These calls change the
+ * links stored in ctx in place, in FP64, and reset G to 1.
+ *
+ * lgf_set_unit_links: U_mu(x) = 1 (a cold start).
+ * lgf_wilson_sweeps: n_heatbath times, one heat-bath sweep at coupling beta >= 0
+ *   for the action beta sum_P (1 - Re Tr U_P / 3) followed by n_overrelax
+ *   overrelaxation sweeps.  A sweep updates every link once: mu = 0..3, for
+ *   each the sites with x+y+z+t even, then odd (links of one such class share
+ *   no plaquette and are updated at once), each link through the SU(2)
+ *   subgroups (0,1), (0,2), (1,2) in turn (heat bath: Kennedy-Pendleton for
+ *   b = 2 beta k/3 >= 1.6, Creutz's method below; overrelaxation: the reflection
+ *   that keeps the local action) and then reunitarised.  Heat-bath sweep i takes
+ *   its random numbers from Philox4x32-10 with key = seed and sweep counter
+ *   first_sweep + i (counter (mu V + s, sweep, 1024 subgroup + draw, 0)), so the
+ *   result does not depend on the launch shape, and splitting a run into calls
+ *   at any heat-bath sweep gives the same links.  n_heatbath = 0 runs
+ *   n_overrelax overrelaxation sweeps alone.  Needs stored links
+ *   (LGF_ERR_STATE); every extent must be even (LGF_ERR_UNSUPPORTED_DIMS).
+ *   Blocks until done.
+ * lgf_plaquette: *P = mean over all plaquettes of Re Tr U_P / 3 of the stored
+ *   links, FP64, summed in a fixed order (the same value on every call).
+ */
+int lgf_set_unit_links(lgf_ctx* ctx);
+int lgf_wilson_sweeps(lgf_ctx* ctx, double beta, unsigned long long seed, int first_sweep, int n_heatbath,
+                      int n_overrelax);
+int lgf_plaquette(lgf_ctx* ctx, double* P);
+
 /* Release all device memory of ctx.  NULL is a no-op. */
 void lgf_destroy(lgf_ctx* ctx);
 

@@ -106,6 +106,7 @@ struct lgf_ctx {
     double2* gl_part = nullptr;
     double2* gl_At = nullptr;  // [16][9]
     double* gl_D = nullptr;    // [5]
+    double* wil_part = nullptr;  // plaquette partial sums, then the result
 };
 
 namespace {
@@ -430,7 +431,7 @@ void free_all(lgf_ctx* c)
     if (c->exec) cudaGraphExecDestroy(c->exec);
     void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
                     c->hist, c->err, c->stage, c->tables, c->mult, c->AH64, c->Fs64, c->AH32, c->Fs32, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
-                    c->gl_part, c->gl_At, c->gl_D};
+                    c->gl_part, c->gl_At, c->gl_D, c->wil_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_ctl) cudaFreeHost(c->host_ctl);
@@ -628,6 +629,12 @@ int ensure_diff(lgf_ctx* c)
     CKR(alloc((void**)&c->dFA, 4 * Vs * sizeof(double2)));
     CKR(alloc((void**)&c->dFB, 4 * Vs * sizeof(double2)));
     return LGF_OK;
+}
+
+int ensure_plaq(lgf_ctx* c)
+{
+    if (c->wil_part) return LGF_OK;
+    return alloc((void**)&c->wil_part, (size_t)(plaquette_blocks(c->V) + 1) * sizeof(double));
 }
 
 int ensure_gluon(lgf_ctx* c)
@@ -1207,6 +1214,55 @@ int lgf_gluon_pmin_bwd(lgf_ctx* c, double gD, double* gU)
     launch_gluon_bwd(c->stream, c->lat, c->U64, c->gl_At, coef, c->tb, c->dGp);
     launch_unpack_planes(c->stream, c->V, c->dGp, gU);
     CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return LGF_OK;
+}
+
+int lgf_set_unit_links(lgf_ctx* c)
+{
+    if (!c) return LGF_ERR_ARG;
+    launch_unit_links(c->stream, c->lat, c->U64);
+    if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_links = true;
+    return LGF_OK;
+}
+
+int lgf_wilson_sweeps(lgf_ctx* c, double beta, unsigned long long seed, int first_sweep, int n_heatbath,
+                      int n_overrelax)
+{
+    if (!c || !(beta >= 0) || !std::isfinite(beta) || first_sweep < 0 || n_heatbath < 0 || n_overrelax < 0)
+        return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    for (int mu = 0; mu < 4; mu++)
+        if (c->L[mu] % 2) return LGF_ERR_UNSUPPORTED_DIMS;  // the checkerboard needs even extents
+    if ((long long)first_sweep + n_heatbath > 0xffffffffLL) return LGF_ERR_ARG;
+    // n_heatbath = 0: overrelaxation sweeps only
+    const int rounds = n_heatbath > 0 ? n_heatbath : 1;
+    for (int i = 0; i < rounds; i++) {
+        const unsigned int sweep = (unsigned int)(first_sweep + i);
+        for (int mode = n_heatbath > 0 ? 0 : 1; mode < 1 + n_overrelax; mode++)
+            for (int mu = 0; mu < 4; mu++)
+                for (int par = 0; par < 2; par++)
+                    launch_wilson(c->stream, c->lat, c->U64, mu, par, mode > 0, beta, seed, sweep);
+        CK(cudaGetLastError());
+    }
+    if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return LGF_OK;
+}
+
+int lgf_plaquette(lgf_ctx* c, double* P)
+{
+    if (!c || !P) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CKR(ensure_plaq(c));
+    const int nb = plaquette_blocks(c->V);
+    launch_plaquette(c->stream, c->lat, c->U64, c->wil_part, c->wil_part + nb);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(P, c->wil_part + nb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LGF_OK;
 }

@@ -1,6 +1,6 @@
 // Host-side launch interface between the C ABI (lgf_capi.cu) and the kernel
 // translation units (lgf_k64.cu: FP64 kernels and the conversion kernels,
-// lgf_k32.cu: FP32 kernels).  Splitting by precision keeps each unit small and
+// lgf_k32.cu: FP32 kernels, lgf_wilson.cu: configuration generation).  Splitting by precision keeps each unit small and
 // lets them compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
@@ -70,6 +70,13 @@ void launch_gluon(cudaStream_t s, const Lat& d, const double2* U, const Tables& 
                   double* D);
 void launch_gluon_bwd(cudaStream_t s, const Lat& d, const double2* U, const double2* At, double coef, const Tables& tb,
                       double2* Gout);
+// Wilson-action heat bath / overrelaxation of one (mu, parity) class of links,
+// and the mean plaquette (lgf_wilson.cu)
+void launch_wilson(cudaStream_t s, const Lat& d, double2* U, int mu, int parity, int overrelax, double beta,
+                   unsigned long long seed, unsigned int sweep);
+void launch_unit_links(cudaStream_t s, const Lat& d, double2* U);
+int plaquette_blocks(int V);
+void launch_plaquette(cudaStream_t s, const Lat& d, const double2* U, double* part, double* out);
 // writes the GPU's global nanosecond timer to *p
 void launch_stamp(cudaStream_t s, unsigned long long* p);
 

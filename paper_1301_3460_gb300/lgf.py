@@ -89,6 +89,9 @@ def load(build_if_missing: bool = True):
             "lgf_step_bwd": ([P, D, P, P], I),
             "lgf_gluon_pmin": ([P, DP, DP], I),
             "lgf_gluon_pmin_bwd": ([P, D, P], I),
+            "lgf_set_unit_links": ([P], I),
+            "lgf_wilson_sweeps": ([P, D, ctypes.c_ulonglong, I, I, I], I),
+            "lgf_plaquette": ([P, DP], I),
             "lgf_batch_create": ([I, ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
             "lgf_batch_set_stream": ([P, P], I),
             "lgf_batch_set_links": ([P, I, P, I], I),
@@ -396,3 +399,28 @@ def fix(U, dims, alpha: float = 0.08, tol: float = 1e-15, max_iter: int = 100000
         lat.set_links(U)
         info = lat.fix(alpha, tol, max_iter)
         return lat.get_links(), lat.get_gauge(), info
+
+
+def _set_unit_links(self):
+    """Store U_mu(x) = 1 (cold start) and reset G."""
+    _check(self._lib.lgf_set_unit_links(self._h), "lgf_set_unit_links")
+
+
+def _wilson_sweeps(self, beta: float, seed: int, first_sweep: int = 0, n_heatbath: int = 1, n_overrelax: int = 0):
+    """Wilson-action Monte Carlo of the stored links on the GPU: n_heatbath times,
+    one heat-bath sweep (random-number sweep counter first_sweep + i) followed by
+    n_overrelax overrelaxation sweeps.  Resets G."""
+    _check(self._lib.lgf_wilson_sweeps(self._h, float(beta), int(seed) & 0xFFFFFFFFFFFFFFFF, int(first_sweep),
+                                       int(n_heatbath), int(n_overrelax)), "lgf_wilson_sweeps")
+
+
+def _plaquette(self) -> float:
+    """Mean Re Tr U_P / 3 over all plaquettes of the stored links."""
+    P = ctypes.c_double()
+    _check(self._lib.lgf_plaquette(self._h, ctypes.byref(P)), "lgf_plaquette")
+    return P.value
+
+
+Lattice.set_unit_links = _set_unit_links
+Lattice.wilson_sweeps = _wilson_sweeps
+Lattice.plaquette = _plaquette
