@@ -55,8 +55,11 @@ def parse():
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-links18", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble"],
-                    help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble")
+    ap.add_argument("--no-wilson", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson"],
+                    help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble; "
+                         "wilson: Wilson-action configuration generation (heat bath + overrelaxation)")
+    ap.add_argument("--beta", type=float, default=6.0, help="coupling of --workload wilson")
     return ap.parse_args()
 
 
@@ -111,6 +114,13 @@ class Clocks:
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        # the sampler's start-up (NVML initialisation) must not fall inside the timed region
+        t0 = time.time()
+        while time.time() - t0 < 15 and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.p is None:
@@ -239,13 +249,14 @@ def run_ours(args, dims):
         lat.set_links(dev[i % len(dev)])
         return lat.fix(args.alpha, args.tol, args.max_iter)
 
+    # the clock sampler starts before the warm-up, so its start-up overlaps untimed work
+    clocks = Clocks(local)
+    clocks.start()
     for k in range(args.warmup):
         step(k)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     info = []
     ev[0].record(stream)
@@ -374,6 +385,41 @@ def run_ours(args, dims):
         diff = {"steps": Kd, "checkpoint_every": every, "fwd_ms": 1000 * (t1 - t0), "bwd_ms": 1000 * (t2 - t1),
                 "fwd_bwd_steps_per_s": Kd / (t2 - t0), "D_pmin": float(D.item())}
 
+    # Wilson-action configuration generation at the same extents (beta = 6.0, cold start)
+    wilson = None
+    if not args.no_wilson:
+        lw = lgf.Lattice(dims, track_gauge=False, stream=stream)
+        lw.set_unit_links()
+        lw.wilson_sweeps(6.0, 7, first_sweep=0, n_heatbath=3, n_overrelax=1)
+        wilson = {"beta": 6.0, "start": "cold + 3 x (heat bath + overrelaxation)", "links_per_sweep": 4 * V}
+        for lab, nhb, nor in (("heatbath", 1, 0), ("overrelax", 0, 1)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.steps):
+                lw.wilson_sweeps(6.0, 7, first_sweep=3 + k, n_heatbath=nhb, n_overrelax=nor)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msw = e0.elapsed_time(e1) / args.steps
+            gf = roofline.WILSON_FLOPS_PER_LINK * 4 * V / msw / 1e6
+            wilson[lab] = {"ms_per_sweep": msw, "gflops": gf, "frac_fp64_peak": gf / FP64_PEAK_GFLOPS}
+        wilson["plaquette"] = lw.plaquette()
+        # generate -> fix on the device: Wilson-action configurations at three couplings
+        # (cold start, 40 x (heat bath + 4 overrelaxation)), then FP64 gauge fixing
+        wilson["fix"] = {}
+        for beta in (5.7, 6.0, 6.2):
+            lw.set_unit_links()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            lw.wilson_sweeps(beta, 11, first_sweep=0, n_heatbath=40, n_overrelax=4)
+            e1.record(stream)
+            r = lw.fix(args.alpha, args.tol, 20000)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            wilson["fix"][str(beta)] = {"generate_ms": e0.elapsed_time(e1), "plaquette": lw.plaquette(),
+                                        "iters": r["iters"], "fix_ms": e1.elapsed_time(e2), "F": r["F"],
+                                        "theta": r["theta"], "converged": r["converged"]}
+        lw.close()
+
     # end to end through the C ABI from pinned host memory, copies included
     e2e = None
     if not args.no_e2e:
@@ -433,6 +479,7 @@ def run_ours(args, dims):
                        "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
                        % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
             "time_to_theta": ttt, "mixed": mixed, "links18": links18, "diff": diff, "plain_sd_16x4": plain,
+            "wilson_generation": wilson,
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
@@ -474,12 +521,12 @@ def run_ensemble(args):
             b.set_links(i, u)
         return b.fix(args.alpha, args.tol, args.max_iter)
 
+    clocks = Clocks(local)
+    clocks.start()
     for _ in range(max(1, args.warmup)):
         r = step()
         log("warm-up step: iters %s" % r["iters"][:4])
     torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = []
     e0.record(stream)
@@ -511,10 +558,104 @@ def run_ensemble(args):
     return 0
 
 
+def run_wilson(args, dims):
+    """Wilson-action configuration generation: one step = one compound sweep (a
+    heat-bath sweep and four overrelaxation sweeps) of every link of the lattice,
+    from a cold start thermalised by the warm-up steps."""
+    import torch
+
+    from paper_1301_3460_gb300 import lgf, roofline
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = tdist
+    lgf.load()
+    V = int(np.prod(dims))
+    stream = torch.cuda.current_stream()
+    n_or = 4
+    lat = lgf.Lattice(dims, track_gauge=False, stream=stream)
+    lat.set_unit_links()
+    seed = 1000 + rank
+    clocks = Clocks(local)
+    clocks.start()
+    for k in range(args.warmup):
+        lat.wilson_sweeps(args.beta, seed, first_sweep=k, n_heatbath=1, n_overrelax=n_or)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        lat.wilson_sweeps(args.beta, seed, first_sweep=args.warmup + k, n_heatbath=1, n_overrelax=n_or)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    T = e0.elapsed_time(e1) / 1000.0
+    T, n = reduce_over_ranks(pg, T, args.steps)
+    # the two kernels on their own: heat-bath and overrelaxation sweeps
+    kinds = {}
+    for lab, nhb, nor in (("heatbath", 1, 0), ("overrelax", 0, 1)):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(3):
+            lat.wilson_sweeps(args.beta, seed, first_sweep=args.warmup + args.steps + k, n_heatbath=nhb,
+                              n_overrelax=nor)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        msw = f0.elapsed_time(f1) / 3
+        gf = roofline.WILSON_FLOPS_PER_LINK * 4 * V / msw / 1e6
+        kinds[lab] = {"ms_per_sweep": msw, "ms_per_launch": msw / 8, "gflops": gf}
+    plaq = lat.plaquette()
+    lat.close()
+    hb = kinds["heatbath"]
+    roof = {"bound": "alu", "kernel": "k_wilson (heat bath)", "achieved": hb["gflops"], "peak": FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s", "frac": hb["gflops"] / FP64_PEAK_GFLOPS, "traffic": None,
+            "peak_source": "GB300 nominal dense FP64; flops per link exclude the sampler's transcendental functions"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        from paper_1301_3460_gb300 import inputs
+
+        Ls = (16, 16, 16, 16)
+        Us = inputs.unit_field(Ls)
+        t0 = time.perf_counter()
+        Us = orc.wilson_sweeps(Ls, Us, args.beta, seed, 1, mode=0)
+        Us = orc.wilson_sweeps(Ls, Us, args.beta, seed, n_or, mode=1)
+        dt = (time.perf_counter() - t0) * V / int(np.prod(Ls))
+        cpu = {"value": 1.0 / dt, "unit": "compound sweeps/s", "cores": 1, "kind": "oracle",
+               "sample": "one compound sweep of a 16^4 lattice from a cold start, scaled by volume to %s"
+               % "x".join(map(str, dims))}
+    if rank == 0:
+        line = {
+            "metric": "Wilson-action compound sweeps/s (1 heat bath + %d overrelaxation)" % n_or,
+            "value": n / T, "unit": "compound sweeps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * T / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "SU(3) %s Wilson action beta=%g, checkerboard SU(2)-subgroup heat bath + "
+                                   "overrelaxation, 12-real links, cold start" % ("x".join(map(str, dims)), args.beta),
+                       "l2": "links larger than L2 (%.0f MB)" % (4 * V * 12 * 8 / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "kernels": kinds, "plaquette": plaq, "roofline": roof, "cpu_baseline": cpu,
+            "gpu_launches": args.steps * 8 * (1 + n_or), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "wilson":
+        dims = tuple(int(v) for v in args.dims.split(","))
+        return run_wilson(args, dims)
     dims = tuple(int(v) for v in args.dims.split(","))
     if args.impl == "reference":
         return run_reference(args, dims)

@@ -265,10 +265,17 @@ static void update_link(const int L[4], cplx* U, long s, int mu, double beta, ui
     reunit_rows(u);
 }
 
-/* One link update on its own (mode as above), for checking single updates */
-void orc_wilson_link(const int L[4], cplx* U, long s, int mu, double beta, uint64_t seed, uint32_t sweep, int mode)
+/* One link update on its own (mode as above), as it would run inside a sweep
+ * on the field U: the new U_mu(s) goes to out (3x3), U is left as it was. */
+void orc_wilson_link(const int L[4], cplx* U, long s, int mu, double beta, uint64_t seed, uint32_t sweep, int mode,
+                     cplx* out)
 {
+    cplx* u = U + ((long)mu * vol(L) + s) * 9;
+    cplx keep[9];
+    memcpy(keep, u, sizeof keep);
     update_link(L, U, s, mu, beta, seed, sweep, mode);
+    memcpy(out, u, sizeof keep);
+    memcpy(u, keep, sizeof keep);
 }
 
 /* One sweep over all links: mu = 0..3, even sites then odd sites. */

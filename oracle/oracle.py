@@ -78,7 +78,7 @@ def _load():
             lib.orc_wilson_plaquette.argtypes = [_int_p, v]
             lib.orc_wilson_plaquette.restype = ctypes.c_double
             lib.orc_wilson_link.argtypes = [_int_p, v, ctypes.c_long, ctypes.c_int, ctypes.c_double, u64, u32,
-                                             ctypes.c_int]
+                                             ctypes.c_int, v]
             lib.orc_philox4x32.argtypes = [v, v, v]
             lib.orc_su2_samples.argtypes = [ctypes.c_double, u64, ctypes.c_int, _dbl_p]
             lib.orc_threads.restype = ctypes.c_int
@@ -250,12 +250,13 @@ def wilson_sweeps(L, U, beta, seed, sweeps, mode=0, first_sweep=0):
 
 
 def wilson_link(L, U, site, mu, beta, seed, sweep, mode=0):
-    """The update of one link U_mu(site) given all other links (as inside a
-    sweep).  Returns new links (input untouched)."""
+    """The update of one link U_mu(site) given all other links, as inside a
+    sweep; returns the new 3x3 link (U is not modified)."""
     d, V = _dims(L)
-    U = _c(U, (4, V, 3, 3)).copy()
-    _load().orc_wilson_link(d, _ptr(U), int(site), int(mu), float(beta), int(seed), int(sweep), int(mode))
-    return U
+    U = _c(U, (4, V, 3, 3))
+    out = np.empty((3, 3), np.complex128)
+    _load().orc_wilson_link(d, _ptr(U), int(site), int(mu), float(beta), int(seed), int(sweep), int(mode), _ptr(out))
+    return out
 
 
 def wilson_plaquette(L, U) -> float:

@@ -119,8 +119,9 @@ bool make_shape(const Lat& d, size_t elem, int nt_xy, int nfc, int nt_zt, int xw
     const int P = d.P;
     if (nfc != 1 && nfc != 2 && nfc != 4) return false;
     if ((size_t)(4 + nfc) * P * elem > budget) return false;
-    const int ZT = d.L[2] * d.L[3];
-    if (xw < 1 || d.L[0] % xw || (size_t)2 * xw * ZT * elem > budget) return false;
+    if (xw < 1 || d.L[0] % xw) return false;
+    const ZtFft Z = make_zt_fft(d.L[2], d.L[3], xw, elem);
+    if (zt_tile_bytes(Z, d.L[3], elem) > budget) return false;
     sh->nt_xy = nt_xy;
     sh->nt_zt = nt_zt;
     XyFft& X = sh->xy;
@@ -131,14 +132,7 @@ bool make_shape(const Lat& d, size_t elem, int nt_xy, int nfc, int nt_zt, int xw
     X.lx = make_lines((unsigned)(nfc * d.L[1]));
     X.ly = make_lines((unsigned)(nfc * d.L[0]));
     X.nfc = nfc;
-    ZtFft& Z = sh->zt;
-    Z.pz = make_axis_plan(d.L[2]);
-    Z.pt = make_axis_plan(d.L[3]);
-    Z.mz = make_linemap((unsigned)xw, (unsigned)(d.L[2] * xw), 1, (unsigned)xw);
-    Z.mt = make_linemap(1u << 30, 0, 1, (unsigned)(d.L[2] * xw));
-    Z.lz = make_lines((unsigned)(xw * d.L[3]));
-    Z.lt = make_lines((unsigned)(xw * d.L[2]));
-    Z.xw = xw;
+    sh->zt = Z;
     return true;
 }
 

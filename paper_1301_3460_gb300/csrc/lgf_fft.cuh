@@ -275,7 +275,32 @@ struct ZtFft {
     LineMap mz, mt;
     Lines lz, lt;     // xw*Lt z-lines, xw*Lz t-lines
     int xw;
+    int rs;           // row stride (values) of the [t][z][xi] tile: Lz*xw, maybe padded
 };
+
+// Plans and maps of the [t][z][xi] pencil tile of xw x-columns.  Consecutive
+// threads take the z-lines of consecutive (xi, t): groups of xw values one row
+// apart.  When a row spans whole 128-byte bank windows and a group does not,
+// the row is padded by xw values so that the groups of consecutive t fall in
+// different banks instead of the same ones.
+inline ZtFft make_zt_fft(int Lz, int Lt, int xw, size_t elem)
+{
+    ZtFft Z{};
+    Z.pz = make_axis_plan(Lz);
+    Z.pt = make_axis_plan(Lt);
+    unsigned rs = (unsigned)(Lz * xw);
+    if ((rs * elem) % 128 == 0 && xw * elem < 128) rs += (unsigned)xw;
+    Z.mz = make_linemap((unsigned)xw, rs, 1, (unsigned)xw);
+    Z.mt = make_linemap(1u << 30, 0, 1, rs);
+    Z.lz = make_lines((unsigned)(xw * Lt));
+    Z.lt = make_lines((unsigned)(xw * Lz));
+    Z.xw = xw;
+    Z.rs = (int)rs;
+    return Z;
+}
+
+// shared memory of the two pencil buffers
+inline size_t zt_tile_bytes(const ZtFft& Z, int Lt, size_t elem) { return (size_t)2 * Lt * Z.rs * elem; }
 
 // The four Delta fields of one xy-plane in a = [f][y][x] (4 P values), with
 // scratch b of nfc P values: transform along x then y, chunk by chunk; the

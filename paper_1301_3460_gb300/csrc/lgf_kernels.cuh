@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, con
 // ---------------------------------------------------------------- k_zt
 
 // One block per (x-chunk of xw columns, y, field).  Shared memory: two buffers of
-// xw * Lz * Lt values laid out [t][z][xi].  Data arrive transformed along x and
+// Lt rows of Z.rs >= xw * Lz values, laid out [t][z][xi].  Data arrive transformed along x and
 // y, so the x and y indices are the momenta kx, ky.
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t<T>* __restrict__ Fd, const Ctl* ctl,
@@ -229,18 +229,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
     if (ld_flag(&ctl->phase_done)) return;
-    const int XW = Z.xw;
+    const int XW = Z.xw, RS = Z.rs;
     const int Lz = d.L[2], Lt = d.L[3], P = d.P;
     const int x0 = blockIdx.x * XW, y = blockIdx.y, f = blockIdx.z;
     vec2_t<T>* base = Fd + (size_t)f * d.V + x0 + d.L[0] * y;
     const int n = XW * Lz * Lt;
+    const int LzXW = Lz * XW;
+    // value i = xi + XW (z + Lz t) of the pencil sits at t RS + (i mod Lz XW) in the tile
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int zt = i / XW, xi = i - zt * XW;
-        sm[i] = base[xi + (size_t)P * zt];
+        const int t = i / LzXW;
+        sm[i + t * (RS - LzXW)] = base[xi + (size_t)P * zt];
     }
     __syncthreads();
     vec2_t<T>* a = sm;
-    vec2_t<T>* b = sm + n;
+    vec2_t<T>* b = sm + (size_t)Lt * RS;
     // forward along z and t
     vec2_t<T>* r = fft_lines<T>(Z.pz, a, b, Z.lz, 1, Z.mz, twz, kFwd);
     r = fft_lines<T>(Z.pt, r, r == a ? b : a, Z.lt, 1, Z.mt, twt, kFwd);
@@ -250,11 +253,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
         const T* mrow = mult + x0 + d.L[0] * y;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int zt = i / XW, xi = i - zt * XW;
+            const int o = i + (i / LzXW) * (RS - LzXW);
             const T m = __ldg(mrow + xi + (size_t)P * zt);
-            vec2_t<T> v = r[i];
+            vec2_t<T> v = r[o];
             v.x *= m;
             v.y *= m;
-            r[i] = v;
+            r[o] = v;
         }
     } else {
         const double inv_v = 1.0 / (double)d.V;
@@ -264,10 +268,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
             const int kt = zt / Lz, kz = zt - kt * Lz;
             const double p2 = s2x[x0 + xi] + sy + s2z[kz] + s2t[kt];
             const T m = (p2 > 0.0) ? (T)(p2max / p2 * inv_v) : (T)0;
-            vec2_t<T> v = r[i];
+            const int o = i + kt * (RS - LzXW);
+            vec2_t<T> v = r[o];
             v.x *= m;
             v.y *= m;
-            r[i] = v;
+            r[o] = v;
         }
     }
     __syncthreads();
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
     r = fft_lines<T>(Z.pz, r, r == a ? b : a, Z.lz, 1, Z.mz, twz, kInv);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int zt = i / XW, xi = i - zt * XW;
-        base[xi + (size_t)P * zt] = r[i];
+        base[xi + (size_t)P * zt] = r[i + (i / LzXW) * (RS - LzXW)];
     }
 }
 

@@ -20,7 +20,7 @@ template <typename T> inline size_t xy_smem(const Lat& d, const Shape& sh)
 }
 template <typename T> inline size_t zt_smem(const Lat& d, const Shape& sh)
 {
-    return (size_t)2 * sh.zt.xw * d.L[2] * d.L[3] * sizeof(vec2_t<T>);
+    return zt_tile_bytes(sh.zt, d.L[3], sizeof(vec2_t<T>));
 }
 
 template <typename K> inline cudaError_t allow_max_smem(K* kernel, int optin)

@@ -88,15 +88,12 @@ extern "C" int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in,
     sh.xy.lx = make_lines((unsigned)dims[1]);
     sh.xy.ly = make_lines((unsigned)dims[0]);
     int xw = 4;
-    while (xw > 1 && (dims[0] % xw || (size_t)2 * xw * d.nplanes * sizeof(double2) > budget)) xw >>= 1;
-    if ((size_t)2 * xw * d.nplanes * sizeof(double2) > budget) return LGF_ERR_UNSUPPORTED_DIMS;
-    sh.zt.pz = make_axis_plan(dims[2]);
-    sh.zt.pt = make_axis_plan(dims[3]);
-    sh.zt.mz = make_linemap((unsigned)xw, (unsigned)(dims[2] * xw), 1, (unsigned)xw);
-    sh.zt.mt = make_linemap(1u << 30, 0, 1, (unsigned)(dims[2] * xw));
-    sh.zt.lz = make_lines((unsigned)(xw * dims[3]));
-    sh.zt.lt = make_lines((unsigned)(xw * dims[2]));
-    sh.zt.xw = xw;
+    while (xw > 1 && (dims[0] % xw ||
+                      zt_tile_bytes(make_zt_fft(dims[2], dims[3], xw, sizeof(double2)), dims[3], sizeof(double2)) >
+                          budget))
+        xw >>= 1;
+    sh.zt = make_zt_fft(dims[2], dims[3], xw, sizeof(double2));
+    if (zt_tile_bytes(sh.zt, dims[3], sizeof(double2)) > budget) return LGF_ERR_UNSUPPORTED_DIMS;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LGF_ERR_CUDA;

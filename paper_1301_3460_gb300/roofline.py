@@ -22,6 +22,19 @@ FP64 path, per site (V sites per launch):
                 G: rebuild (42) + one product (132).
 FP32 kernels move half the bytes of every array they keep in FP32 (links, G, g,
 fields, packed parts, multiplier); their flop counts are the same.
+
+Wilson-action generation (k_wilson, one launch per direction and checkerboard
+parity), per link updated, with full 3x3 complex products of 198 flops (27
+complex multiplies, 18 complex adds) and 216 when accumulated into a sum:
+  staples   6 products + 6 accumulated products               2484
+  W = U A   one product                                          198
+  subgroups 3 x (projection 20, R 56, rotation of two rows of U
+            and of W 168)                                        732
+  reunit    Gram-Schmidt of two rows and the row-2 rebuild       100
+  total                                                         3514
+The sampler's transcendental functions (heat bath) are not counted.  Bytes: a
+launch reads about the whole link field (7/8 of it) and writes V/2 links, far
+below what the FP64 pipe takes to do the arithmetic: the kernel is ALU-bound.
 """
 from __future__ import annotations
 
@@ -50,3 +63,6 @@ def per_iteration(dims, precision: int = 64) -> dict:
         V *= int(v)
     ps = per_site(dims, precision)
     return dict(bytes=V * sum(k["bytes"] for k in ps.values()), flops=V * sum(k["flops"] for k in ps.values()))
+
+
+WILSON_FLOPS_PER_LINK = 3514

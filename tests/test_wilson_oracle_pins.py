@@ -118,3 +118,19 @@ def test_weak_coupling_expansion():
     beta = 30.0
     p = _plaquette_chain((4, 4, 4, 4), beta, 30, 60)
     assert abs(p - (1 - 2 / beta - 1.2208 / beta ** 2)) < 0.001
+
+
+def test_single_link_update_matches_sweep():
+    """Link (mu = 0, even site) is the first kind a sweep updates, so its update
+    on the starting field is what the sweep leaves there; the single-link entry
+    leaves its input untouched."""
+    L = (4, 4, 4, 4)
+    U = inputs.rough_gauge_field(L, 0.4, seed=8)
+    U1 = oracle.wilson_sweeps(L, U, 5.7, 4, 1, first_sweep=3)
+    before = U.copy()
+    for s in (0, 2, 5, 255 - 3):  # even sites: parity of x+y+z+t
+        c = np.unravel_index(s, L[::-1])[::-1]
+        if sum(c) % 2:
+            continue
+        assert np.abs(oracle.wilson_link(L, U, s, 0, 5.7, 4, 3) - U1[0, s]).max() < 1e-15
+    assert np.array_equal(U, before)
