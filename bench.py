@@ -405,19 +405,36 @@ def run_ours(args, dims):
         wilson["plaquette"] = lw.plaquette()
         # generate -> fix on the device: Wilson-action configurations at three couplings
         # (cold start, 40 x (heat bath + 4 overrelaxation)), then FP64 gauge fixing
+        # and the same configurations in mixed precision (FP32 until theta < 1e-6)
         wilson["fix"] = {}
+        lm = None if args.no_mixed else lgf.Lattice(dims, mixed=True, stream=stream)
         for beta in (5.7, 6.0, 6.2):
             lw.set_unit_links()
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
             e0.record(stream)
             lw.wilson_sweeps(beta, 11, first_sweep=0, n_heatbath=40, n_overrelax=4)
             e1.record(stream)
-            r = lw.fix(args.alpha, args.tol, 20000)
+            U_gen = lw.get_links(device="cuda") if lm is not None else None
             e2.record(stream)
+            r = lw.fix(args.alpha, args.tol, 20000)
+            e3.record(stream)
             torch.cuda.synchronize()
-            wilson["fix"][str(beta)] = {"generate_ms": e0.elapsed_time(e1), "plaquette": lw.plaquette(),
-                                        "iters": r["iters"], "fix_ms": e1.elapsed_time(e2), "F": r["F"],
-                                        "theta": r["theta"], "converged": r["converged"]}
+            w = {"generate_ms": e0.elapsed_time(e1), "plaquette": lw.plaquette(), "iters": r["iters"],
+                 "fix_ms": e2.elapsed_time(e3), "F": r["F"], "theta": r["theta"], "converged": r["converged"]}
+            if lm is not None:
+                lm.set_links(U_gen)
+                del U_gen
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                rm = lm.fix(args.alpha, args.tol, 20000)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                w["mixed"] = {"iters_fp32": rm["iters_fp32"], "iters_fp64": rm["iters_fp64"],
+                              "fix_ms": f0.elapsed_time(f1), "F": rm["F"], "converged": rm["converged"],
+                              "F_rel_diff_vs_fp64": abs(rm["F"] / r["F"] - 1) if r["F"] else None}
+            wilson["fix"][str(beta)] = w
+        if lm is not None:
+            lm.close()
         lw.close()
 
     # end to end through the C ABI from pinned host memory, copies included

@@ -148,8 +148,8 @@ int lgf_build_g(lgf_ctx* ctx, const double* Dt_in, double alpha, double* g_out, 
 /*
  * lgf_time_kernels (instrumentation): run n_iter iterations of the loop body on
  * the stored links, launching the kernels one by one on the context's stream
- * with CUDA events around each launch, and write to ms[4] the mean duration
- * (milliseconds) of (0) the Delta + x,y FFT kernel, (1) the z,t FFT +
+ * with CUDA events around each launch, and write to ms[4] the median over the
+ * iterations of the duration (milliseconds) of (0) the Delta + x,y FFT kernel, (1) the z,t FFT +
  * accelerator kernel, (2) the inverse x,y FFT + g kernel, (3) the update
  * kernel.  precision 64 times the FP64 kernels; 32 the FP32 kernels (mixed
  * contexts only; they start from an FP32 copy of the stored links).  The stored

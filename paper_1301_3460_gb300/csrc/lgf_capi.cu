@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <array>
 #include <cstring>
 #include <map>
@@ -962,7 +963,7 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
     CKR(reset_stage_ctl(c, alpha));
     cudaEvent_t ev[5];
     for (int i = 0; i < 5; i++) CK(cudaEventCreate(&ev[i]));
-    double acc[4] = {0, 0, 0, 0};
+    std::vector<float> samples[4];
     cudaStream_t s = c->stream;
     int rc = LGF_OK;
     if (precision == 32) {
@@ -1005,13 +1006,20 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
         for (int k = 0; k < 4; k++) {
             float t = 0;
             cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
-            acc[k] += t;
+            samples[k].push_back(t);
         }
     }
     for (int i = 0; i < 5; i++) cudaEventDestroy(ev[i]);
     if (rc != LGF_OK) return rc;
     CK(cudaGetLastError());
-    for (int k = 0; k < 4; k++) ms[k] = acc[k] / n_iter;
+    // median over the iterations: a launch delayed by the host (the events bracket
+    // the enqueue as well as the kernel) shows up as an outlier, not in the median
+    for (int k = 0; k < 4; k++) {
+        std::vector<float>& v = samples[k];
+        std::sort(v.begin(), v.end());
+        const size_t n = v.size();
+        ms[k] = (n % 2) ? v[n / 2] : 0.5 * ((double)v[n / 2 - 1] + (double)v[n / 2]);
+    }
     return LGF_OK;
 }
 
