@@ -60,6 +60,8 @@ def parse():
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble; "
                          "wilson: Wilson-action configuration generation (heat bath + overrelaxation)")
     ap.add_argument("--beta", type=float, default=6.0, help="coupling of --workload wilson")
+    ap.add_argument("--switch-tol", type=float, default=1e-6,
+                    help="theta that ends the FP32 phase of --workload ensemble (1e-6 as specified; 1e-13 deep)")
     return ap.parse_args()
 
 
@@ -313,6 +315,21 @@ def run_ours(args, dims):
                                     F_rel_diff_vs_fp64=(abs(r["F"] / f64 - 1) if f64 else None)))
         mixed = {"value": mit / Tm, "unit": "iters/s", "ms_per_step": 1000 * Tm / args.steps,
                  "speedup_time_to_theta_vs_fp64": T / Tm, "time_to_theta": mttt}
+        # the FP32 phase run down to theta < 1e-13, where FP32 iterations stop tracking FP64 ones
+        latm.set_switch_tol(1e-13)
+        deep = {}
+        for e, Ud in zip((str(v) for v in EPS), dev):
+            latm.set_links(Ud)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            r = latm.fix(args.alpha, args.tol, args.max_iter)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            f64 = ttt.get(e, {}).get("F")
+            deep[e] = dict(iters_fp32=r["iters_fp32"], iters_fp64=r["iters_fp64"], ms=f0.elapsed_time(f1),
+                           converged=r["converged"], F_rel_diff_vs_fp64=(abs(r["F"] / f64 - 1) if f64 else None))
+        mixed["time_to_theta_switch_1e-13"] = deep
+        latm.set_switch_tol(1e-6)
         latm.set_links(dev[1])
         msm = latm.time_kernels(args.alpha, n_iter=8, precision=32)
         per32 = roofline.per_site(dims, 32)
@@ -423,7 +440,6 @@ def run_ours(args, dims):
                  "fix_ms": e2.elapsed_time(e3), "F": r["F"], "theta": r["theta"], "converged": r["converged"]}
             if lm is not None:
                 lm.set_links(U_gen)
-                del U_gen
                 f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 f0.record(stream)
                 rm = lm.fix(args.alpha, args.tol, 20000)
@@ -432,6 +448,17 @@ def run_ours(args, dims):
                 w["mixed"] = {"iters_fp32": rm["iters_fp32"], "iters_fp64": rm["iters_fp64"],
                               "fix_ms": f0.elapsed_time(f1), "F": rm["F"], "converged": rm["converged"],
                               "F_rel_diff_vs_fp64": abs(rm["F"] / r["F"] - 1) if r["F"] else None}
+                # FP32 phase down to theta < 1e-13
+                lm.set_switch_tol(1e-13)
+                lm.set_links(U_gen)
+                f0.record(stream)
+                rd = lm.fix(args.alpha, args.tol, 20000)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                lm.set_switch_tol(1e-6)
+                w["mixed_switch_1e-13"] = {"iters_fp32": rd["iters_fp32"], "iters_fp64": rd["iters_fp64"],
+                                        "fix_ms": f0.elapsed_time(f1), "F": rd["F"], "converged": rd["converged"],
+                                        "F_rel_diff_vs_fp64": abs(rd["F"] / r["F"] - 1) if r["F"] else None}
             wilson["fix"][str(beta)] = w
         if lm is not None:
             lm.close()
@@ -531,6 +558,7 @@ def run_ensemble(args):
     log("generated %d lattices" % len(dev))
     stream = torch.cuda.current_stream()
     b = lgf.Batch(dims, mixed=True, stream=stream)
+    b.set_switch_tol(args.switch_tol)
     log("batch created")
 
     def step():
@@ -562,7 +590,8 @@ def run_ensemble(args):
         "ms_per_step": 1000 * T / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32->f64", "data": "synthetic",
         "config": {"workload": "ensemble 32x16^4 + 16x24^4 + 8x32^3x64 + 2x48^3x96, mixed precision, one graph "
-                               "launch per step, eps U[0.15,0.5]", "sites": sites, "lattices": len(dims)},
+                               "launch per step, eps U[0.15,0.5]", "sites": sites, "lattices": len(dims),
+                   "switch_tol": args.switch_tol},
         "time_to_theta_ms": {"p50": float(np.percentile(tt, 50)), "p99": float(np.percentile(tt, 99)),
                              "max": float(tt.max())},
         "all_converged": all(s == lgf.LGF_OK for r in res for s in r["status"]),

@@ -128,7 +128,15 @@ int lgf_get_stats(lgf_ctx* ctx, int* iters_fp32, int* iters_fp64);
  */
 int lgf_set_loop_bound(lgf_ctx* ctx, int max_body_runs);
 
-/* Threshold on theta that ends the FP32 phase of LGF_MIXED (default 1e-6). */
+/*
+ * Threshold on theta that ends the FP32 phase of LGF_MIXED (default 1e-6).
+ * The FP32 phase also ends when FP32 arithmetic stops improving theta: 50
+ * iterations without a new smallest theta once theta < 1e-12 (FP32's floor is
+ * near 1e-14 on the lattices measured), 2000 iterations above that.  FP32
+ * iterations track FP64 ones down to theta ~1e-13, so switch_tol = 1e-13 leaves
+ * the FP64 finish only the error of the re-projection to remove; switch_tol = 0
+ * runs the FP32 phase down to its floor.
+ */
 int lgf_set_switch_tol(lgf_ctx* ctx, double switch_tol);
 
 /*
@@ -188,6 +196,7 @@ int lgf_autotune(lgf_ctx* ctx);
 typedef struct lgf_batch lgf_batch;
 int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out);
 int lgf_batch_set_stream(lgf_batch* b, void* cuda_stream);
+int lgf_batch_set_switch_tol(lgf_batch* b, double switch_tol);  /* every lattice, as lgf_set_switch_tol */
 int lgf_batch_set_links(lgf_batch* b, int i, const double* U, int on_device);
 int lgf_batch_fix(lgf_batch* b, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta,
                   int* status, double* t_retire_ms);

@@ -49,6 +49,13 @@ void set_error(const char* what, cudaError_t e, const char* file, int line)
     } while (0)
 
 constexpr int kHistCap = 65536;
+// FP32 phase: iterations without a new smallest theta before FP64 takes over.
+// Far from FP32's floor (theta ~1e-14..1e-13 on 32^4) a long window, because the
+// method's theta is not monotone (FP64 runs on Wilson-action configurations go up
+// to ~1200 iterations between new minima); near it a short one.
+constexpr int kStallIters = 2000;
+constexpr int kStallNearIters = 50;
+constexpr double kNearFloor = 1e-12;
 
 bool length_ok(int L)
 {
@@ -710,6 +717,11 @@ Ctl initial_ctl(const lgf_ctx* c, double alpha, double tol, int max_iter)
     h.phase = c->mixed ? 0 : 1;
     h.hist_cap = kHistCap;
     h.loop_bound = c->loop_bound;
+    h.theta_best = 1.0e300;
+    h.iter_best = 0;
+    h.stall = c->mixed ? kStallIters : 0;
+    h.stall_near = kStallNearIters;
+    h.near_floor = kNearFloor;
     return h;
 }
 
@@ -786,7 +798,7 @@ int lgf_set_loop_bound(lgf_ctx* c, int max_body_runs)
 
 int lgf_set_switch_tol(lgf_ctx* c, double tol)
 {
-    if (!c || !(tol > 0)) return LGF_ERR_ARG;
+    if (!c || !(tol >= 0)) return LGF_ERR_ARG;
     c->switch_tol = tol;
     return LGF_OK;
 }
@@ -1076,6 +1088,13 @@ int lgf_batch_set_stream(lgf_batch* b, void* stream)
     if (!b) return LGF_ERR_ARG;
     b->stream = reinterpret_cast<cudaStream_t>(stream);
     for (lgf_ctx* c : b->ctx) c->stream = b->stream;
+    return LGF_OK;
+}
+
+int lgf_batch_set_switch_tol(lgf_batch* b, double tol)
+{
+    if (!b || !(tol >= 0)) return LGF_ERR_ARG;
+    for (lgf_ctx* c : b->ctx) c->switch_tol = tol;
     return LGF_OK;
 }
 

@@ -156,6 +156,11 @@ struct Ctl {
     unsigned int body_runs;
     int hist_cap;
     unsigned int loop_bound;  // extra cap on body runs of a device loop (0: none)
+    double theta_best;     // smallest theta of the FP32 phase so far
+    int iter_best;         // the iteration that reached it
+    int stall;             // FP32 phase ends after this many iterations without a new smallest theta (0: never) ...
+    int stall_near;        // ... or after this many once theta_best < near_floor
+    double near_floor;
 };
 
 }  // namespace lgf

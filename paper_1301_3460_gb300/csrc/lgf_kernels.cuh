@@ -94,6 +94,14 @@ static __device__ void reduce_theta_F(double th, double f, double* __restrict__ 
         } else if (it >= ctl->max_iter) {
             ctl->phase_done = 1;
             ctl->done = 1;
+        } else if (ctl->phase == 0 && ctl->stall > 0) {
+            // FP32 arithmetic has stopped improving theta: hand over to FP64
+            if (theta < ctl->theta_best) {
+                ctl->theta_best = theta;
+                ctl->iter_best = it;
+            } else if (it - ctl->iter_best >= (ctl->theta_best < ctl->near_floor ? ctl->stall_near : ctl->stall)) {
+                ctl->phase_done = 1;
+            }
         }
         ctl->ticket = 0u;
         __threadfence();

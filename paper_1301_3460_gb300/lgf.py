@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
             "lgf_batch_create": ([I, ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
             "lgf_batch_set_stream": ([P, P], I),
             "lgf_batch_set_links": ([P, I, P, I], I),
+            "lgf_batch_set_switch_tol": ([P, D], I),
             "lgf_batch_fix": ([P, D, D, I, IP, DP, DP, IP, DP], I),
             "lgf_batch_get_links": ([P, I, P, I], I),
             "lgf_batch_get_gauge": ([P, I, P, I], I),
@@ -357,6 +358,9 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_switch_tol(self, tol: float):
+        _check(self._lib.lgf_batch_set_switch_tol(self._h, float(tol)), "lgf_batch_set_switch_tol")
 
     def set_links(self, i: int, U):
         p, dev, keep = _in_ptr(U, (4, self.V[i], 3, 3))

@@ -71,3 +71,35 @@ def test_mixed_max_iter_in_fp32_phase_keeps_progress():
     _, th0, F0 = orc.delta(L, U)
     _, th3, F3 = orc.delta(L, Um)
     assert F3 > F0
+
+
+@pytest.mark.parametrize("switch", [1e-13, 0.0])
+@pytest.mark.parametrize("L,seed", [((16, 16, 16, 16), 1601), ((8, 8, 8, 8), 1001)])
+def test_deep_fp32_phase(L, seed, switch):
+    """A deep FP32 phase: to theta < 1e-13, or (switch_tol = 0) until FP32
+    stops improving theta (50 iterations without a new smallest value near its
+    floor); then the FP64 finish.  The result is the FP64 oracle's maximum all
+    the same."""
+    U = inputs.rough_gauge_field(L, 0.3, seed)
+    ref = orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=5000)
+    with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_links(U)
+        r6 = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+        lat.set_switch_tol(switch)
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+        hist = lat.history()
+        Um, G = lat.get_links(), lat.get_gauge()
+    assert r["converged"] and r["theta"] < 1e-15
+    assert r["iters_fp32"] > r6["iters_fp32"] and r["iters_fp64"] <= r6["iters_fp64"]
+    assert r["iters_fp32"] < 5000
+    th32 = hist[: r["iters_fp32"], 0]
+    assert th32.min() < 1e-9  # far below the default switch
+    assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+    np.testing.assert_allclose(orc.gauge_transform(L, U, G), Um, atol=1e-13)
+    with pytest.raises(lgf.LgfError):
+        lat2 = lgf.Lattice(L, mixed=True)
+        try:
+            lat2.set_switch_tol(-1.0)
+        finally:
+            lat2.close()
