@@ -140,6 +140,14 @@ int lgf_set_loop_bound(lgf_ctx* ctx, int max_body_runs);
 int lgf_set_switch_tol(lgf_ctx* ctx, double switch_tol);
 
 /*
+ * LGF_MIXED: every `every` FP32 updates (default 25; 0 = never) G is
+ * re-orthonormalised and the FP32 links are rebuilt from the input links as
+ * G(x) U_in(x) G^dag(x+mu), so that FP32 rounding does not accumulate along a
+ * long FP32 phase: the drift would otherwise be left for the FP64 finish.
+ */
+int lgf_set_fp32_refresh(lgf_ctx* ctx, int every);
+
+/*
  * Stage entry points (same arithmetic as inside lgf_fix, exposed for checking
  * each step on its own).  All arrays are caller-owned, layouts as above.
  *

@@ -278,6 +278,101 @@ static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restri
     }
 }
 
+// ---------------------------------------------------------------- FP32-phase refresh
+//
+// The FP32 links drift off the input's gauge orbit by FP32 rounding at every
+// update, and the drift grows with the iteration count; at the switch the FP64
+// links are rebuilt on the orbit from G, so the FP64 finish has to remove
+// whatever the FP32 links had drifted.  Every `every` FP32 updates the links are
+// therefore rebuilt from the input and the (re-orthonormalised) G:
+//   G(x) <- reunit(G(x)),  U32_mu(x) <- G(x) U_in_mu(x) G^dag(x+mu)
+// with the packed anti-Hermitian parts and Re Tr of the new links for Delta.
+
+__device__ __forceinline__ bool refresh_due(const Ctl* ctl, int every)
+{
+    if (ld_flag(&ctl->phase_done) || ctl->phase != 0) return false;
+    return every > 0 && ctl->iter > 0 && ctl->iter % every == 0;
+}
+
+// rows 0,1 of G32 re-orthonormalised (Gram-Schmidt in FP64)
+static __global__ void k_refresh_g(int V, float2* __restrict__ G32, const Ctl* ctl, int every)
+{
+    if (!refresh_due(ctl, every)) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    cx<double> X[6], g[9];
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        const float2 v = G32[(size_t)e * V + s];
+        X[e] = mk<double>((double)v.x, (double)v.y);
+    }
+    reunit_rows(X, g);
+#pragma unroll
+    for (int e = 0; e < 6; e++) G32[(size_t)e * V + s] = make_float2((float)g[e].re, (float)g[e].im);
+}
+
+// U32 = G U_in G^dag(x+mu) in FP32 from the FP64 input links (ne64 stored entries)
+static __global__ void __launch_bounds__(256) k_refresh_u(Lat d, int ne64, const double2* __restrict__ U64,
+                                                          const float2* __restrict__ G32, float2* __restrict__ U32,
+                                                          float2* __restrict__ AH, float* __restrict__ Fs,
+                                                          const Ctl* ctl, int every)
+{
+    if (!refresh_due(ctl, every)) return;
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    int c[4];
+    site_coords(d, s, c);
+    cx<float> gx[9];
+#pragma unroll
+    for (int e = 0; e < 6; e++) gx[e] = ld<float>(G32 + (size_t)e * V + s);
+    complete_row2(gx, gx + 6);
+    float f = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        cx<float> u[9];
+#pragma unroll
+        for (int e = 0; e < 6; e++) {
+            const double2 v = __ldg(U64 + (size_t)(mu * ne64 + e) * V + s);
+            u[e] = mk<float>((float)v.x, (float)v.y);
+        }
+        complete_row2(u, u + 6);
+        cx<float> A[6];
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<float> acc = cmul(gx[3 * i], u[j]);
+                acc = cmac(acc, gx[3 * i + 1], u[3 + j]);
+                acc = cmac(acc, gx[3 * i + 2], u[6 + j]);
+                A[3 * i + j] = acc;
+            }
+        const int sn = site_shift(d, s, c[mu], mu, +1);
+        cx<float> gn[9];
+#pragma unroll
+        for (int e = 0; e < 6; e++) gn[e] = ld<float>(G32 + (size_t)e * V + sn);
+        complete_row2(gn, gn + 6);
+        cx<float> w[9];
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<float> acc = cmulc(A[3 * i], gn[3 * j]);
+                acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
+                acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
+                w[3 * i + j] = acc;
+                st<float>(U32 + (size_t)(mu * 6 + 3 * i + j) * V + s, acc);
+            }
+        complete_row2(w, w + 6);
+        cx<float> a[4];
+        ah_pack(w, a);
+#pragma unroll
+        for (int k = 0; k < 4; k++) st<float>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
+        f += w[0].re + w[4].re + w[8].re;
+    }
+    Fs[s] = f;
+}
+
 // hand over from the FP32 phase to the FP64 phase
 static __global__ void k_phase_switch(Ctl* ctl)
 {

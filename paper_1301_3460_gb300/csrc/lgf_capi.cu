@@ -49,6 +49,7 @@ void set_error(const char* what, cudaError_t e, const char* file, int line)
     } while (0)
 
 constexpr int kHistCap = 65536;
+constexpr int kRefreshEvery = 25;
 // FP32 phase: iterations without a new smallest theta before FP64 takes over.
 // Far from FP32's floor (theta ~1e-14..1e-13 on 32^4) a long window, because the
 // method's theta is not monotone (FP64 runs on Wilson-action configurations go up
@@ -101,6 +102,7 @@ struct lgf_ctx {
     Ctl* host_ctl = nullptr;  // pinned
     bool have_links = false;
     double switch_tol = 1e-6;
+    int refresh_every = kRefreshEvery;  // FP32 phase: rebuild U32 from U_in and G every this many updates (0: never)
     unsigned int loop_bound = 0;  // test hook: cap on loop-body runs
     cudaGraphExec_t exec = nullptr;
     int last_iters = 0, last_iters32 = 0, last_hist = 0;
@@ -182,6 +184,8 @@ void launch_body(lgf_ctx* c, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, vec2_t<
         launch_xyinv_g<T>(d, sh, c->tb, s, Fd, g, c->ctl);
     }
     launch_update<T>(d, s, U, G, g, c->ctl, ah_of<T>(c), fs_of<T>(c));
+    if (sizeof(T) == 4 && c->refresh_every > 0)
+        launch_refresh32(s, c->lat32, c->lat.ne, c->U64, c->G32, c->U32, c->AH32, c->Fs32, c->ctl, c->refresh_every);
     launch_delta<T>(d, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl, c->hist, !c->plain);
 }
 
@@ -800,6 +804,16 @@ int lgf_set_switch_tol(lgf_ctx* c, double tol)
 {
     if (!c || !(tol >= 0)) return LGF_ERR_ARG;
     c->switch_tol = tol;
+    return LGF_OK;
+}
+
+int lgf_set_fp32_refresh(lgf_ctx* c, int every)
+{
+    if (!c || every < 0) return LGF_ERR_ARG;
+    if (every != c->refresh_every) {
+        c->refresh_every = every;
+        drop_graph(c);  // the interval is a launch argument of the captured body
+    }
     return LGF_OK;
 }
 

@@ -46,6 +46,12 @@ void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs,
     k_project<<<blocks(d.V, 256), 256, 0, s>>>(d, U64, G64, Gs, ctl);
     k_phase_switch<<<1, 1, 0, s>>>(ctl);
 }
+void launch_refresh32(cudaStream_t s, const Lat& d32, int ne64, const double2* U64, float2* G32, float2* U32,
+                      float2* AH32, float* Fs32, const Ctl* ctl, int every)
+{
+    k_refresh_g<<<blocks(d32.V, 256), 256, 0, s>>>(d32.V, G32, ctl, every);
+    k_refresh_u<<<blocks(d32.V, 256), 256, 0, s>>>(d32, ne64, U64, G32, U32, AH32, Fs32, ctl, every);
+}
 static __global__ void k_stamp(unsigned long long* p)
 {
     unsigned long long t;

@@ -56,6 +56,9 @@ void launch_mixed_prep(cudaStream_t s, int V, int ne, const double2* U64, float2
 void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
                    Ctl* ctl);
 void launch_loop_ctl(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h);
+// FP32 phase: every `every` updates, G re-orthonormalised and U32 rebuilt as G U_in G^dag
+void launch_refresh32(cudaStream_t s, const Lat& d32, int ne64, const double2* U64, float2* G32, float2* U32,
+                      float2* AH32, float* Fs32, const Ctl* ctl, int every);
 void launch_make_mult(cudaStream_t s, const Lat& d, const Tables& tb, double* m64, float* m32);
 // derivative of one step and of the gluon propagator (lgf_diff.cuh)
 void launch_g_from_dt(cudaStream_t s, int V, const double2* Fd, double2* g, double alpha);

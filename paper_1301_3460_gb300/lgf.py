@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True):
             "lgf_get_history": ([P, DP, I, IP], I),
             "lgf_get_stats": ([P, IP, IP], I),
             "lgf_set_switch_tol": ([P, D], I),
+            "lgf_set_fp32_refresh": ([P, I], I),
             "lgf_set_loop_bound": ([P, I], I),
             "lgf_delta": ([P, P, I, DP, DP], I),
             "lgf_accelerate": ([P, P, P, I], I),
@@ -199,6 +200,9 @@ class Lattice:
 
     def set_switch_tol(self, tol: float):
         _check(self._lib.lgf_set_switch_tol(self._h, float(tol)), "lgf_set_switch_tol")
+
+    def set_fp32_refresh(self, every: int):
+        _check(self._lib.lgf_set_fp32_refresh(self._h, int(every)), "lgf_set_fp32_refresh")
 
     def set_links(self, U):
         p, dev, keep = _in_ptr(U, (4, self.V, 3, 3))

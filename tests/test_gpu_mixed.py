@@ -103,3 +103,27 @@ def test_deep_fp32_phase(L, seed, switch):
             lat2.set_switch_tol(-1.0)
         finally:
             lat2.close()
+
+
+def test_fp32_refresh_keeps_the_fp32_links_on_the_orbit():
+    """Rebuilding the FP32 links from the input and G during the FP32 phase
+    (every 5 updates here) leaves much less for the FP64 finish to remove: theta
+    right after the switch drops, and the result is the oracle's either way."""
+    L, seed = (16, 16, 16, 16), 1601
+    U = inputs.rough_gauge_field(L, 0.3, seed)
+    ref = orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=5000)
+    after = {}
+    with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_switch_tol(1e-13)
+        for every in (0, 5):
+            lat.set_fp32_refresh(every)
+            lat.set_links(U)
+            r = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+            assert r["converged"]
+            assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+            after[every] = lat.history()[r["iters_fp32"], 0]
+            np.testing.assert_allclose(orc.gauge_transform(L, U, lat.get_gauge()), lat.get_links(), atol=1e-13)
+        with pytest.raises(lgf.LgfError):
+            lat.set_fp32_refresh(-1)
+    print("theta after the switch: no refresh %.3e, every 5: %.3e" % (after[0], after[5]))
+    assert after[5] < 0.2 * after[0]
