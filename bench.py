@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-links18", action="store_true")
+    ap.add_argument("--no-links8", action="store_true")
     ap.add_argument("--no-wilson", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble; "
@@ -362,6 +363,35 @@ def run_ours(args, dims):
         links18 = {"value": n18 / T18, "unit": "iters/s", "ms_per_step": 1000 * T18 / args.steps,
                    "update_ms": ms18["update"], "kernels_ms": ms18}
 
+    # the 8-real form: a third of the 12-real link bytes, more FP64 work per load and store
+    links8 = None
+    if not args.no_links18 and not args.no_links8:
+        l8 = lgf.Lattice(dims, links8=True, stream=stream)
+        n8, T8, ok8 = 0, 0.0, True
+        try:
+            for Ud in dev:
+                l8.set_links(Ud)
+        except lgf.LgfError:
+            ok8 = False  # a link too close to the form's singular set |u00| = 1
+        if ok8:
+            l8.autotune()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.steps):
+                l8.set_links(dev[k % len(dev)])
+                n8 += l8.fix(args.alpha, args.tol, args.max_iter)["iters"]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            T8 = e0.elapsed_time(e1) / 1000.0
+            l8.set_links(dev[1])
+            ms8 = l8.time_kernels(args.alpha, n_iter=8, precision=64)
+            links8 = {"value": n8 / T8, "unit": "iters/s", "ms_per_step": 1000 * T8 / args.steps,
+                      "update_ms": ms8["update"], "kernels_ms": ms8}
+        else:
+            links8 = {"value": None, "note": "configuration refused: a link the 8-real form cannot hold"}
+        l8.close()
+
     # critical slowing down: plain steepest descent against the accelerated method at 16^4
     plain = None
     if not args.no_plain:
@@ -522,7 +552,8 @@ def run_ours(args, dims):
             "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol,
                        "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
                        % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
-            "time_to_theta": ttt, "mixed": mixed, "links18": links18, "diff": diff, "plain_sd_16x4": plain,
+            "time_to_theta": ttt, "mixed": mixed, "links18": links18, "links8": links8, "diff": diff,
+            "plain_sd_16x4": plain,
             "wilson_generation": wilson,
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,

@@ -61,6 +61,13 @@ typedef enum {
 #define LGF_LINKS18 8     /* keep row 2 of each FP64 link in memory (18 reals) instead of rebuilding it on
                              every load (12 reals): the same values (row 2 is stored as the rebuild from
                              rows 0,1), 50% more link bytes, fewer FP64 operations per update */
+#define LGF_LINKS8 16     /* keep each FP64 link in its 8-real form (u01, u02, u10 and the phases of u00 and
+                             u20; the rest rebuilt from unitarity and det = 1 on every load): a third of the
+                             12-real bytes, two sqrt, two sincos and a division more per load, two atan2 per
+                             store.  Singular where |u00| = 1 and accurate to ~1e-15/(|u01|^2 + |u02|^2) near
+                             it: lgf_set_links also rejects links it cannot hold to 1e-10 (LGF_ERR_NOT_SU3),
+                             and the configuration generator (unit links) is not available (LGF_ERR_STATE).
+                             Exclusive with LGF_LINKS18 */
 #define LGF_PLAIN_SD 4    /* steepest descent without Fourier acceleration: g = reunit(1 + alpha/2 Delta);
                              the method whose critical slowing down the introduction cites (alpha < 0.125
                              for stability with this Delta normalisation) */
@@ -70,7 +77,7 @@ typedef enum {
  * Each extent must be one of 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128 and the
  * plane sizes must satisfy Lx*Ly <= 3072 and Lz*Lt <= 12288 (the FFT tiles are
  * held in shared memory); else LGF_ERR_UNSUPPORTED_DIMS.  flags: LGF_FP64 or
- * LGF_MIXED, optionally | LGF_NO_GAUGE, | LGF_PLAIN_SD, | LGF_LINKS18.  *out receives the
+ * LGF_MIXED, optionally | LGF_NO_GAUGE, | LGF_PLAIN_SD, | LGF_LINKS18 or | LGF_LINKS8.  *out receives the
  * context.
  */
 int lgf_create(const int dims[4], int flags, lgf_ctx** out);
@@ -221,6 +228,9 @@ void lgf_batch_destroy(lgf_batch* b);
  * follow G = dL/dRe U + i dL/dIm U, i.e. dL = Re sum conj(G) dU.  Arrays are
  * device pointers, complex128 [4][V][3][3] like the links.
  *
+ * lgf_step_fwd: one Fourier-accelerated step: U_out = the links after one
+ *   update of U_in (checked and stored as lgf_set_links does); the stored links
+ *   are then U_out and G holds g of the step.
  * lgf_step_bwd: the stored links are the step's input U (rows 0,1 used, row 2
  *   rebuilt); gU_out is the cotangent of the step's output U' (all three rows,
  *   row 2 taken as its rebuild from rows 0,1); gU_in receives the cotangent of
@@ -231,6 +241,7 @@ void lgf_batch_destroy(lgf_batch* b);
  *   gets the four values.
  * lgf_gluon_pmin_bwd: gU = gD * dD/dU of the stored links (row 2 zero).
  */
+int lgf_step_fwd(lgf_ctx* ctx, double alpha, const double* U_in, double* U_out);
 int lgf_step_bwd(lgf_ctx* ctx, double alpha, const double* gU_out, double* gU_in);
 int lgf_gluon_pmin(lgf_ctx* ctx, double* D, double* Dp);
 int lgf_gluon_pmin_bwd(lgf_ctx* ctx, double gD, double* gU);

@@ -23,25 +23,41 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double 
 }
 
 // Interleaved [4][V][3][3] complex128 -> rows 0,1 planes of T; optional SU(3)
-// check of the full input matrix: err[0] = max |U U^dag - 1|, err[1] = max |det U - 1|.
+// check of the full input matrix: err[0] = max |U U^dag - 1|, err[1] = max |det U - 1|,
+// err[2] = max error of the round trip through the 8-real form (ne = 4).
 template <typename T>
 static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in, vec2_t<T>* __restrict__ U,
                              unsigned long long* err, int validate)
 {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;  // link index mu*V + s
-    double e_unit = 0.0, e_det = 0.0;
+    double e_unit = 0.0, e_det = 0.0, e_form = 0.0;
     if (idx < 4L * V) {
         const int mu = (int)(idx / V), s = (int)(idx - (long)mu * V);
         const double* p = in + idx * 18;
         cx<double> m[9];
 #pragma unroll
         for (int e = 0; e < 9; e++) m[e] = mk<double>(p[2 * e], p[2 * e + 1]);
+        if (ne == 4) {
+            // 8-real form; the check below also covers its round trip (the form
+            // cannot hold links with |u00| = 1, such as the unit matrix)
+            cx<T> w[9];
 #pragma unroll
-        for (int e = 0; e < 6; e++) {
-            vec2_t<T> v;
-            v.x = (T)m[e].re;
-            v.y = (T)m[e].im;
-            U[(size_t)(mu * ne + e) * V + s] = v;
+            for (int e = 0; e < 9; e++) w[e] = mk<T>((T)m[e].re, (T)m[e].im);
+            store_link<T>(U, V, 4, mu, s, w);
+            if (validate) {
+                cx<T> r[9];
+                rebuild8<T>(w[1], w[2], w[3], atan2(w[0].im, w[0].re), atan2(w[6].im, w[6].re), r);
+#pragma unroll
+                for (int e = 0; e < 9; e++) e_form = dmax_nan(e_form, (double)sqrt(norm2(r[e] - w[e])));
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 6; e++) {
+                vec2_t<T> v;
+                v.x = (T)m[e].re;
+                v.y = (T)m[e].im;
+                U[(size_t)(mu * ne + e) * V + s] = v;
+            }
         }
         if (ne == 9) {
             // row 2 stored as the rebuild from rows 0,1, as a 12-real load would give it
@@ -78,10 +94,12 @@ static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in
         for (int o = 16; o > 0; o >>= 1) {
             e_unit = dmax_nan(e_unit, __shfl_down_sync(0xffffffffu, e_unit, o));
             e_det = dmax_nan(e_det, __shfl_down_sync(0xffffffffu, e_det, o));
+            e_form = dmax_nan(e_form, __shfl_down_sync(0xffffffffu, e_form, o));
         }
         if ((threadIdx.x & 31) == 0) {
             atomic_max_nonneg(err, e_unit);
             atomic_max_nonneg(err + 1, e_det);
+            atomic_max_nonneg(err + 2, e_form);
         }
     }
 }
@@ -187,12 +205,12 @@ static __global__ void k_mixed_prep(int V, int ne, const double2* __restrict__ U
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
 #pragma unroll
-    for (int mu = 0; mu < 4; mu++)
+    for (int mu = 0; mu < 4; mu++) {
+        cx<double> u[9];
+        load_link<double>(U64, V, ne, mu, s, u);
 #pragma unroll
-        for (int e = 0; e < 6; e++) {
-            const double2 v = U64[(size_t)(mu * ne + e) * V + s];
-            U32[(size_t)(mu * 6 + e) * V + s] = make_float2((float)v.x, (float)v.y);
-        }
+        for (int e = 0; e < 6; e++) U32[(size_t)(mu * 6 + e) * V + s] = make_float2((float)u[e].re, (float)u[e].im);
+    }
 #pragma unroll
     for (int e = 0; e < 6; e++) G32[(size_t)e * V + s] = make_float2((e == 0 || e == 4) ? 1.f : 0.f, 0.f);
 }
@@ -253,13 +271,9 @@ static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restri
                 acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
                 acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
                 w[3 * i + j] = acc;
-                st<double>(U + (size_t)(mu * d.ne + 3 * i + j) * V + s, acc);
             }
-        if (d.ne == 9) {
-            complete_row2(w, w + 6);
-#pragma unroll
-            for (int e = 6; e < 9; e++) st<double>(U + (size_t)(mu * 9 + e) * V + s, w[e]);
-        }
+        complete_row2(w, w + 6);
+        store_link<double>(U, V, d.ne, mu, s, w);
     }
     if (G != nullptr) {
         cx<double> Gm[9];
@@ -331,10 +345,11 @@ static __global__ void __launch_bounds__(256) k_refresh_u(Lat d, int ne64, const
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         cx<float> u[9];
+        {
+            cx<double> ud[9];
+            load_link<double>(U64, V, ne64, mu, s, ud);
 #pragma unroll
-        for (int e = 0; e < 6; e++) {
-            const double2 v = __ldg(U64 + (size_t)(mu * ne64 + e) * V + s);
-            u[e] = mk<float>((float)v.x, (float)v.y);
+            for (int e = 0; e < 6; e++) u[e] = mk<float>((float)ud[e].re, (float)ud[e].im);
         }
         complete_row2(u, u + 6);
         cx<float> A[6];

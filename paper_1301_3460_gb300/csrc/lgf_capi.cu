@@ -50,6 +50,11 @@ void set_error(const char* what, cudaError_t e, const char* file, int line)
 
 constexpr int kHistCap = 65536;
 constexpr int kRefreshEvery = 25;
+// The 8-real form's rebuild divides by n2 = |u01|^2 + |u02|^2, so it holds a link
+// to about 1e-15 / n2; among the 4 million links of a random 32^4 field the
+// smallest n2 is ~5e-4, so 1e-10 accepts such fields and refuses links within
+// n2 ~ 1e-5 of the form's singular set.
+constexpr double kForm8Tol = 1e-10;
 // FP32 phase: iterations without a new smallest theta before FP64 takes over.
 // Far from FP32's floor (theta ~1e-14..1e-13 on 32^4) a long window, because the
 // method's theta is not monotone (FP64 runs on Wilson-action configurations go up
@@ -393,7 +398,7 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     d.V = c->V;
     d.P = dims[0] * dims[1];
     d.nplanes = dims[2] * dims[3];
-    d.ne = (flags & LGF_LINKS18) ? 9 : 6;
+    d.ne = (flags & LGF_LINKS18) ? 9 : (flags & LGF_LINKS8) ? 4 : 6;
     c->lat32 = d;
     c->lat32.ne = 6;
     if (!pick_shape(d, sizeof(double2), 2, 4, &c->sh64)) return LGF_ERR_UNSUPPORTED_DIMS;
@@ -424,7 +429,7 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     CKR(alloc((void**)&c->ctl, sizeof(Ctl)));
     CKR(alloc((void**)&c->ctl_stage, sizeof(Ctl)));
     CKR(alloc((void**)&c->hist, kHistCap * sizeof(double2)));
-    CKR(alloc((void**)&c->err, 2 * sizeof(unsigned long long)));
+    CKR(alloc((void**)&c->err, 3 * sizeof(unsigned long long)));
     CK(cudaMemset(c->ctl, 0, sizeof(Ctl)));
     CK(cudaMemset(c->ctl_stage, 0, sizeof(Ctl)));
     CK(cudaMallocHost((void**)&c->host_ctl, sizeof(Ctl)));
@@ -765,7 +770,8 @@ int lgf_create(const int dims[4], int flags, lgf_ctx** out)
 {
     if (!dims || !out) return LGF_ERR_ARG;
     *out = nullptr;
-    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD | LGF_LINKS18)) return LGF_ERR_ARG;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD | LGF_LINKS18 | LGF_LINKS8)) return LGF_ERR_ARG;
+    if ((flags & LGF_LINKS18) && (flags & LGF_LINKS8)) return LGF_ERR_ARG;
     lgf_ctx* c = new (std::nothrow) lgf_ctx();
     if (!c) return LGF_ERR_ARG;
     int r = create_impl(dims, flags, c);
@@ -824,17 +830,19 @@ int lgf_set_links(lgf_ctx* c, const double* U, int on_device)
     const double* src;
     c->have_links = false;
     CKR(stage_in(c, U, bytes, on_device, &src));
-    CK(cudaMemsetAsync(c->err, 0, 2 * sizeof(unsigned long long), c->stream));
+    CK(cudaMemsetAsync(c->err, 0, 3 * sizeof(unsigned long long), c->stream));
     launch_pack_links64(c->stream, c->V, c->lat.ne, src, c->U64, c->err);
     if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
     CK(cudaGetLastError());
-    unsigned long long e[2];
+    unsigned long long e[3];
     CK(cudaMemcpyAsync(e, c->err, sizeof e, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    double eu, ed;
+    double eu, ed, ef;
     memcpy(&eu, &e[0], sizeof eu);
     memcpy(&ed, &e[1], sizeof ed);
+    memcpy(&ef, &e[2], sizeof ef);
     if (!(eu < 1e-12) || !(ed < 1e-12)) return LGF_ERR_NOT_SU3;
+    if (!(ef < kForm8Tol)) return LGF_ERR_NOT_SU3;  // 8-real form only (0 otherwise)
     c->have_links = true;
     return LGF_OK;
 }
@@ -1059,7 +1067,8 @@ int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out)
 {
     if (n < 1 || !dims || !out) return LGF_ERR_ARG;
     *out = nullptr;
-    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD | LGF_LINKS18)) return LGF_ERR_ARG;
+    if (flags & ~(LGF_MIXED | LGF_NO_GAUGE | LGF_PLAIN_SD | LGF_LINKS18 | LGF_LINKS8)) return LGF_ERR_ARG;
+    if ((flags & LGF_LINKS18) && (flags & LGF_LINKS8)) return LGF_ERR_ARG;
     lgf_batch* b = new (std::nothrow) lgf_batch();
     if (!b) return LGF_ERR_ARG;
     int r = LGF_OK;
@@ -1192,6 +1201,18 @@ int lgf_batch_get_stats(lgf_batch* b, int i, int* iters_fp32, int* iters_fp64)
     return lgf_get_stats(b->ctx[i], iters_fp32, iters_fp64);
 }
 
+int lgf_step_fwd(lgf_ctx* c, double alpha, const double* U_in, double* U_out)
+{
+    if (!c || !U_in || !U_out || !(alpha > 0)) return LGF_ERR_ARG;
+    CKR(lgf_set_links(c, U_in, 1));
+    int it = 0;
+    const int r = lgf_fix(c, alpha, 0.0, 1, &it, nullptr, nullptr);
+    // theta_tol = 0 is never met: one update and NOT_CONVERGED is the expected outcome
+    if (r != LGF_ERR_NOT_CONVERGED && r != LGF_OK) return r;
+    if (it != 1) return LGF_ERR_STATE;
+    return lgf_get_links(c, U_out, 1);
+}
+
 int lgf_step_bwd(lgf_ctx* c, double alpha, const double* gU_out, double* gU_in)
 {
     if (!c || !gU_out || !gU_in || !(alpha > 0)) return LGF_ERR_ARG;
@@ -1256,6 +1277,7 @@ int lgf_gluon_pmin_bwd(lgf_ctx* c, double gD, double* gU)
 int lgf_set_unit_links(lgf_ctx* c)
 {
     if (!c) return LGF_ERR_ARG;
+    if (c->lat.ne == 4) return LGF_ERR_STATE;  // the 8-real form cannot hold the unit matrix
     launch_unit_links(c->stream, c->lat, c->U64);
     if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
     CK(cudaGetLastError());
@@ -1269,7 +1291,7 @@ int lgf_wilson_sweeps(lgf_ctx* c, double beta, unsigned long long seed, int firs
 {
     if (!c || !(beta >= 0) || !std::isfinite(beta) || first_sweep < 0 || n_heatbath < 0 || n_overrelax < 0)
         return LGF_ERR_ARG;
-    if (!c->have_links) return LGF_ERR_STATE;
+    if (!c->have_links || c->lat.ne == 4) return LGF_ERR_STATE;  // the generator keeps 12 or 18 reals
     for (int mu = 0; mu < 4; mu++)
         if (c->L[mu] % 2) return LGF_ERR_UNSUPPORTED_DIMS;  // the checkerboard needs even extents
     if ((long long)first_sweep + n_heatbath > 0xffffffffLL) return LGF_ERR_ARG;

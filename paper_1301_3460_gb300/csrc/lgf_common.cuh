@@ -103,6 +103,35 @@ template <typename T> __device__ __forceinline__ void complete_row2(const cx<T>*
     r2[2] = cdet2c(m[0], m[4], m[1], m[3]);
 }
 
+// 8-real form of an SU(3) matrix: u01, u02, u10 and the phases of u00 and u20.
+// Unitarity and det = 1 give the rest: |u00|^2 = 1 - n2 with n2 = |u01|^2 +
+// |u02|^2, |u20|^2 = n2 - |u10|^2 (column 0 normalised); rows 0 and 1 orthogonal
+// and conj(row0 x row1) = row 2 are two linear equations for u11, u12 with
+// determinant n2:
+//   u11 = -(t u01 + conj(u02 u20)) / n2,  u12 = (conj(u01 u20) - u02 t) / n2,
+//   t = u10 conj(u00);
+// row 2 is then rebuilt as conj(row0 x row1).  Singular where n2 = 0 (|u00| = 1).
+template <typename T>
+__device__ __forceinline__ void rebuild8(cx<T> a01, cx<T> a02, cx<T> a10, T th0, T th2, cx<T>* u)
+{
+    const T n2 = norm2(a01) + norm2(a02);
+    const T m00 = sqrt(fmax(T(1) - n2, T(0)));
+    const T m20 = sqrt(fmax(n2 - norm2(a10), T(0)));
+    T s0, c0, s2, c2;
+    sincos(th0, &s0, &c0);
+    sincos(th2, &s2, &c2);
+    const cx<T> u00 = mk(m00 * c0, m00 * s0), u20 = mk(m20 * c2, m20 * s2);
+    const T inv = T(1) / n2;
+    const cx<T> t = cmulc(a10, u00);
+    u[0] = u00;
+    u[1] = a01;
+    u[2] = a02;
+    u[3] = a10;
+    u[4] = (cmul(t, a01) + conjg(cmul(a02, u20))) * (-inv);
+    u[5] = (conjg(cmul(a01, u20)) - cmul(a02, t)) * inv;
+    complete_row2(u, u + 6);
+}
+
 // ---------------------------------------------------------------- lattice
 
 // Site index s = x + Lx*(y + Ly*(z + Lz*t)).  An xy-plane is the Lx*Ly block of
@@ -113,8 +142,9 @@ struct Lat {
     int V;
     int P;         // Lx*Ly
     int nplanes;   // Lz*Lt
-    int ne;        // complex entries stored per link: 6 (rows 0,1; row 2 rebuilt on load)
-                   // or 9 (row 2 kept as written, the rebuild done once when stored)
+    int ne;        // complex entries stored per link: 6 (rows 0,1; row 2 rebuilt on load),
+                   // 9 (row 2 kept as written, the rebuild done once when stored) or
+                   // 4 (the 8-real form, FP64 only: u01, u02, u10, phases of u00 and u20)
 };
 
 __device__ __forceinline__ int site_shift(const Lat& d, int s, int c_mu, int mu, int dir)

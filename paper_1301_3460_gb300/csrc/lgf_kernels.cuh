@@ -111,10 +111,19 @@ static __device__ void reduce_theta_F(double th, double f, double* __restrict__ 
 // ---------------------------------------------------------------- link loads
 
 // link (mu, s), layout [mu][ne][V]: rows 0,1 and row 2 (rebuilt as conj(r0 x r1)
-// when ne = 6, read when ne = 9, in which case it was stored as that rebuild)
+// when ne = 6, read when ne = 9, in which case it was stored as that rebuild), or
+// the whole matrix rebuilt from its 8-real form (ne = 4, FP64)
 template <typename T>
 __device__ __forceinline__ void load_link(const vec2_t<T>* __restrict__ U, int V, int ne, int mu, int s, cx<T>* u)
 {
+    if constexpr (sizeof(T) == 8) {
+        if (ne == 4) {
+            const vec2_t<T>* p = U + (size_t)(mu * 4) * V + s;
+            const vec2_t<T> th = __ldg(p + 3 * (size_t)V);
+            rebuild8<T>(ld<T>(p), ld<T>(p + V), ld<T>(p + 2 * (size_t)V), th.x, th.y, u);
+            return;
+        }
+    }
 #pragma unroll
     for (int e = 0; e < 6; e++) u[e] = ld<T>(U + (size_t)(mu * ne + e) * V + s);
     if (ne == 9) {
@@ -122,6 +131,31 @@ __device__ __forceinline__ void load_link(const vec2_t<T>* __restrict__ U, int V
         for (int e = 6; e < 9; e++) u[e] = ld<T>(U + (size_t)(mu * 9 + e) * V + s);
     } else {
         complete_row2(u, u + 6);
+    }
+}
+
+// store link (mu, s) from its full matrix w in the layout of ne (see load_link)
+template <typename T>
+__device__ __forceinline__ void store_link(vec2_t<T>* __restrict__ U, int V, int ne, int mu, int s, const cx<T>* w)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (ne == 4) {
+            vec2_t<T>* p = U + (size_t)(mu * 4) * V + s;
+            st<T>(p, w[1]);
+            st<T>(p + V, w[2]);
+            st<T>(p + 2 * (size_t)V, w[3]);
+            vec2_t<T> th;
+            th.x = atan2(w[0].im, w[0].re);
+            th.y = atan2(w[6].im, w[6].re);
+            p[3 * (size_t)V] = th;
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 6; e++) st<T>(U + (size_t)(mu * ne + e) * V + s, w[e]);
+    if (ne == 9) {
+#pragma unroll
+        for (int e = 6; e < 9; e++) st<T>(U + (size_t)(mu * 9 + e) * V + s, w[e]);
     }
 }
 
@@ -462,13 +496,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
                 acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
                 acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
                 w[3 * i + j] = acc;
-                st<T>(U + (size_t)(mu * d.ne + 3 * i + j) * V + s, acc);
             }
         complete_row2(w, w + 6);
-        if (d.ne == 9) {
-#pragma unroll
-            for (int e = 6; e < 9; e++) st<T>(U + (size_t)(mu * 9 + e) * V + s, w[e]);
-        }
+        store_link<T>(U, V, d.ne, mu, s, w);
         cx<T> a[4];
         ah_pack(w, a);
 #pragma unroll

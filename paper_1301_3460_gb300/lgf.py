@@ -34,6 +34,7 @@ LGF_MIXED = 1
 LGF_NO_GAUGE = 2
 LGF_PLAIN_SD = 4
 LGF_LINKS18 = 8
+LGF_LINKS8 = 16
 
 _lock = threading.Lock()
 _lib = None
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = True):
             "lgf_time_kernels": ([P, D, I, I, DP], I),
             "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
             "lgf_autotune": ([P], I),
+            "lgf_step_fwd": ([P, D, P, P], I),
             "lgf_step_bwd": ([P, D, P, P], I),
             "lgf_gluon_pmin": ([P, DP, DP], I),
             "lgf_gluon_pmin_bwd": ([P, D, P], I),
@@ -152,7 +154,7 @@ class Lattice:
     """One gauge field on the GPU and its gauge-fixing state (an lgf_ctx)."""
 
     def __init__(self, dims, mixed: bool = False, track_gauge: bool = True, stream=None, accelerate: bool = True,
-                 links18: bool = False):
+                 links18: bool = False, links8: bool = False):
         lib = load()
         self.dims = tuple(int(v) for v in dims)
         self.V = int(np.prod(self.dims))
@@ -161,6 +163,8 @@ class Lattice:
             flags |= LGF_PLAIN_SD
         if links18:
             flags |= LGF_LINKS18
+        if links8:
+            flags |= LGF_LINKS8
         arr = (ctypes.c_int * 4)(*self.dims)
         h = ctypes.c_void_p()
         _check(lib.lgf_create(arr, flags, ctypes.byref(h)), "lgf_create")
@@ -295,6 +299,19 @@ def _autotune(self) -> None:
 Lattice.autotune = _autotune
 
 
+def _step_fwd(self, U_in, alpha: float = 0.08):
+    """One Fourier-accelerated step of U_in (contiguous complex128 CUDA tensor
+    (4, V, 3, 3)); returns the new links (the context then holds them)."""
+    import torch
+
+    assert _is_torch(U_in) and U_in.is_cuda and U_in.dtype == torch.complex128
+    U_in = U_in.contiguous()
+    U_out = torch.empty_like(U_in)
+    _check(self._lib.lgf_step_fwd(self._h, float(alpha), ctypes.c_void_p(U_in.data_ptr()),
+                                  ctypes.c_void_p(U_out.data_ptr())), "lgf_step_fwd")
+    return U_out
+
+
 def _step_bwd(self, g_out, alpha: float = 0.08):
     """Cotangent of the stored links (the step's input) from the cotangent g_out of
     the step's output; both contiguous complex128 CUDA tensors (4, V, 3, 3)."""
@@ -324,6 +341,7 @@ def _gluon_pmin_bwd(self, gD: float = 1.0, device="cuda"):
     return g
 
 
+Lattice.step_fwd = _step_fwd
 Lattice.step_bwd = _step_bwd
 Lattice.gluon_pmin = _gluon_pmin
 Lattice.gluon_pmin_bwd = _gluon_pmin_bwd

@@ -127,3 +127,19 @@ def test_unrolled_gradient_finite_differences_16():
     lat.close()
     print("16^4 K=50, 20 directions: worst relative difference to FD: h=1e-6 2nd order %.2e, "
           "h=1e-4 4th order %.2e" % (w2, w4))
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 4, 8, 4)])
+def test_step_fwd_matches_oracle(L):
+    """lgf_step_fwd (the forward of one step, device pointers) against one oracle step."""
+    from oracle import oracle as orc
+
+    U = inputs.rough_gauge_field(L, 0.4, 23)
+    ref = orc.fix(L, U, alpha=0.08, tol=0.0, max_iter=1)
+    with lgf.Lattice(L) as lat:
+        out = lat.step_fwd(torch.from_numpy(U).to("cuda"), 0.08)
+        again = lat.step_fwd(out, 0.08)
+    assert ref["iters"] == 1
+    assert np.max(np.abs(out.cpu().numpy() - ref["U"])) < 1e-13
+    ref2 = orc.fix(L, ref["U"], alpha=0.08, tol=0.0, max_iter=1)
+    assert np.max(np.abs(again.cpu().numpy() - ref2["U"])) < 1e-13
