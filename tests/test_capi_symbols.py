@@ -44,3 +44,44 @@ def test_oracle_builds():
     from oracle import oracle
 
     assert os.path.exists(oracle.build())
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/lgf.h is a C header (C99 and C++17, warnings as errors) and a C
+    program that calls the boundary links against the library; without a GPU
+    lgf_create must fail with a status, not abort."""
+    import shutil
+    import subprocess
+
+    from paper_1301_3460_gb300 import build
+
+    lib = build.build()
+    src = tmp_path / "use_lgf.c"
+    src.write_text(
+        '#include "lgf.h"\n'
+        "#include <stdio.h>\n"
+        "int main(void) {\n"
+        "    int dims[4] = {8, 8, 8, 8};\n"
+        "    lgf_ctx* ctx = 0;\n"
+        "    int rc = lgf_create(dims, LGF_FP64, &ctx);\n"
+        '    printf("%d %s\\n", rc, lgf_strerror(rc));\n'
+        "    if (rc == LGF_OK) lgf_destroy(ctx);\n"
+        "    return 0;\n"
+        "}\n")
+    inc = os.path.join(ROOT, "include")
+    for cc, std in (("gcc", "-std=c99"), ("g++", "-std=c++17")):
+        if shutil.which(cc) is None:
+            continue
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x",
+                            "c" if cc == "gcc" else "c++", os.path.join(inc, "lgf.h")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    exe = tmp_path / "use_lgf"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe), lib,
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    import torch
+
+    if not torch.cuda.is_available():
+        out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+        assert out.returncode == 0
+        assert out.stdout.split()[0] == "2"  # LGF_ERR_CUDA
