@@ -98,3 +98,32 @@ def test_cuda_generator_is_su3():
     with lgf.Lattice(L) as lat:
         lat.set_links(U)
         assert lat.fix(tol=1e-15, max_iter=3000)["converged"]
+
+
+def test_full_ensemble():
+    """The benchmark's ensemble at full size (32 x 16^4, 16 x 24^4, 8 x 32^3x64,
+    2 x 48^3x96, eps uniform in [0.15, 0.5], mixed precision, one graph launch):
+    every lattice converges; a 16^4 and a 24^4 member agree with the FP64 oracle;
+    the 32^3x64 members' links are the gauge transform of their inputs by G."""
+    torch = pytest.importorskip("torch")
+    sizes = ((32, (16, 16, 16, 16)), (16, (24, 24, 24, 24)), (8, (32, 32, 32, 64)), (2, (48, 48, 48, 96)))
+    dims = [d for n, d in sizes for _ in range(n)]
+    eps = np.random.default_rng(5000).uniform(0.15, 0.5, size=len(dims))
+    dev = [inputs.rough_gauge_field_cuda(d, float(e), 5000 + i) for i, (d, e) in enumerate(zip(dims, eps))]
+    with lgf.Batch(dims, mixed=True) as b:
+        for i, u in enumerate(dev):
+            b.set_links(i, u)
+        r = b.fix(alpha=0.08, tol=1e-15, max_iter=20000)
+        assert all(s == lgf.LGF_OK for s in r["status"]) and r["rc"] == lgf.LGF_OK
+        assert max(r["theta"]) < 1e-15
+        for i in (0, 32):
+            L, U = dims[i], dev[i].cpu().numpy()
+            ref = orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=5000)
+            assert r["F"][i] == pytest.approx(ref["F"], rel=1e-12)
+            np.testing.assert_allclose(orc.gauge_transform(L, U, b.get_gauge(i)), b.get_links(i), atol=1e-13)
+        for i in (48, 55):
+            L = dims[i]
+            np.testing.assert_allclose(orc.gauge_transform(L, dev[i].cpu().numpy(), b.get_gauge(i)),
+                                       b.get_links(i), atol=1e-13)
+    del dev
+    torch.cuda.empty_cache()
