@@ -101,12 +101,15 @@ int lgf_set_links(lgf_ctx* ctx, const double* U, int on_device);
  * Outputs (each may be NULL): *iters = updates applied, *F and *theta of the
  * final links.  They are valid also when the call returns LGF_ERR_NOT_CONVERGED
  * or LGF_ERR_NAN.  In LGF_MIXED mode the FP32 phase runs while theta >=
- * switch_tol; then G is reprojected onto SU(3) in FP64 and the links are rebuilt
- * as U = G U_in G^dag(x+mu) in FP64 before the FP64 phase.  Blocks until done.
+ * switch_tol and FP32 keeps improving theta (lgf_set_switch_tol), its links
+ * rebuilt from the input every few updates (lgf_set_fp32_refresh); then G is
+ * reprojected onto SU(3) in FP64 and the links are rebuilt as
+ * U = G U_in G^dag(x+mu) in FP64 before the FP64 phase.  Blocks until done.
  */
 int lgf_fix(lgf_ctx* ctx, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta);
 
-/* lgf_get_links: write the current links, rows 0,1 as stored and row 2 rebuilt. */
+/* lgf_get_links: write the current links as full matrices (row 2 rebuilt as
+ * conj(row0 x row1) for the 12-real form, the whole matrix for the 8-real form). */
 int lgf_get_links(lgf_ctx* ctx, double* U_out, int on_device);
 
 /*
