@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--alpha", type=float, default=0.08)
     ap.add_argument("--tol", type=float, default=1e-15)
     ap.add_argument("--max-iter", type=int, default=20000)
-    ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations of the CPU-baseline sample")
+    ap.add_argument("--cpu-iters", type=int, default=20, help="oracle iterations of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -532,16 +532,40 @@ def run_ours(args, dims):
         pass
     kernels = {k: {"ms": ms[k], "gflops": per[k]["flops"] * V / ms[k] / 1e6, "gbs": per[k]["bytes"] * V / ms[k] / 1e6}
                for k in ms}
+    # the metric's "% of HBM peak": algorithmic bytes of one whole FP64 iteration at the measured rate
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        it_bytes = roofline.per_iteration(dims, 64)["bytes"]
+        hbm_iter = {"bytes_per_iteration": it_bytes, "achieved_gbs": it_bytes * value / 1e9, "peak_gbs": hbm,
+                    "frac": it_bytes * value / 1e9 / hbm,
+                    "note": "FP64 iteration bound by the FP64 pipe, not by HBM; see roofline"}
+        if mixed is not None and "kernels_fp32" in mixed:
+            for k, v in mixed["kernels_fp32"].items():
+                v["hbm_frac_of_measured"] = v["gbs"] / hbm
+    except (OSError, ValueError, KeyError):
+        hbm_iter = None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle as orc
+
+        from paper_1301_3460_gb300 import inputs
 
         t0 = time.perf_counter()
         r = orc.fix(dims, host[1], alpha=args.alpha, tol=0.0, max_iter=args.cpu_iters)
         dt = time.perf_counter() - t0
         cpu = {"value": r["iters"] / dt, "unit": "iters/s", "cores": orc.threads(), "kind": "oracle",
                "sample": "first %d iterations of the eps=0.3 %s configuration" % (r["iters"], "x".join(map(str, dims)))}
+        # whole fixes where the oracle finishes in seconds, and the full-size one derived
+        # from the GPU's iteration count
+        for Ls, seed in (((8, 8, 8, 8), 1001), ((16, 16, 16, 16), 1601)):
+            Us = inputs.rough_gauge_field(Ls, 0.3, seed)
+            t0 = time.perf_counter()
+            rs = orc.fix(Ls, Us, alpha=args.alpha, tol=args.tol, max_iter=args.max_iter)
+            cpu["time_to_theta_%s_s" % "x".join(map(str, Ls))] = {"s": time.perf_counter() - t0, "iters": rs["iters"]}
+        it03 = ttt.get(str(EPS[1]), {}).get("iters")
+        if it03:
+            cpu["time_to_theta_%s_derived_s" % "x".join(map(str, dims))] = it03 * dt / r["iters"]
 
     lat.close()
     if rank == 0:
@@ -555,7 +579,7 @@ def run_ours(args, dims):
             "time_to_theta": ttt, "mixed": mixed, "links18": links18, "links8": links8, "diff": diff,
             "plain_sd_16x4": plain,
             "wilson_generation": wilson,
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "kernels": kernels, "hbm_iteration": hbm_iter, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
