@@ -74,9 +74,11 @@ typedef enum {
 
 /*
  * lgf_create: allocate a context for a lattice of extents dims[4].
- * Each extent must be one of 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128 and the
- * plane sizes must satisfy Lx*Ly <= 3072 and Lz*Lt <= 12288 (the FFT tiles are
- * held in shared memory); else LGF_ERR_UNSUPPORTED_DIMS.  flags: LGF_FP64 or
+ * Each extent must be one of 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, and the
+ * shared-memory FFT tiles (the four fields of one xy-plane plus one of scratch,
+ * and two buffers of one z,t pencil) must fit in 220 KiB: for FP64 and mixed
+ * contexts Lx*Ly <= 2816 and Lt*(Lz + 1) <= 7040 (e.g. 96x24 planes, 64x96 or
+ * 128x48 pencils); else LGF_ERR_UNSUPPORTED_DIMS.  flags: LGF_FP64 or
  * LGF_MIXED, optionally | LGF_NO_GAUGE, | LGF_PLAIN_SD, | LGF_LINKS18 or | LGF_LINKS8.  *out receives the
  * context.
  */

@@ -235,3 +235,51 @@ def test_pinned_host_buffers_match_pageable():
         assert lat._lib.lgf_get_gauge(lat._h, lgf.ctypes.c_void_p(gout.data_ptr()), 0) == 0
     assert np.max(np.abs(out.numpy() - pageable)) == 0.0
     assert np.max(np.abs(gout.numpy() - Gp)) == 0.0
+
+
+# every FFT length the kernels take, along each axis, on thin lattices the oracle runs in
+# seconds; the last two are the largest planes and pencils the FP64 tiles hold
+# (Lx Ly = 2304 of at most 2816, Lt (Lz + 1) = 6240 of at most 7040)
+LONG_AXES = [(128, 4, 4, 4), (4, 96, 4, 4), (4, 4, 64, 4), (4, 4, 4, 128), (48, 6, 4, 4), (4, 4, 24, 48),
+             (16, 4, 96, 4), (96, 24, 4, 4), (4, 4, 64, 96)]
+
+
+@pytest.mark.parametrize("L", LONG_AXES)
+def test_long_axes_links_after_steps(L):
+    U = field(L, eps=0.3, seed=12)
+    ref = orc.fix(L, U, alpha=0.08, tol=0.0, max_iter=3)
+    with lgf.Lattice(L) as lat:
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=0.0, max_iter=3)
+        Ug, Gg = lat.get_links(), lat.get_gauge()
+    assert r["iters"] == 3
+    assert np.max(np.abs(Ug - ref["U"])) < 1e-13
+    assert np.max(np.abs(Gg - ref["G"])) < 1e-13
+    assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+
+
+def test_over_the_plane_limits_is_refused():
+    for L in [(128, 32, 4, 4), (128, 24, 4, 4), (4, 4, 128, 128), (4, 4, 128, 96)]:
+        with pytest.raises(lgf.LgfError) as e:
+            lgf.Lattice(L)
+        assert e.value.status == lgf.LGF_ERR_UNSUPPORTED_DIMS
+
+
+def test_degenerate_stops():
+    """max_iter = 0 measures and stops; a tolerance above theta stops at once; a
+    field already in Landau gauge (U = 1) stops with theta = 0 and F = 1."""
+    L = (8, 8, 8, 8)
+    U = field(L, eps=0.3, seed=13)
+    _, th0, f0 = orc.delta(L, U)
+    with lgf.Lattice(L) as lat:
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=0)
+        assert r["iters"] == 0 and r["status"] == lgf.LGF_ERR_NOT_CONVERGED
+        assert r["theta"] == pytest.approx(th0, rel=1e-12) and r["F"] == pytest.approx(f0, rel=1e-12)
+        assert np.array_equal(lat.get_links(), lat.get_links())
+        np.testing.assert_allclose(lat.get_links(), U, atol=1e-15)
+        r = lat.fix(alpha=0.08, tol=10 * th0, max_iter=100)
+        assert r["iters"] == 0 and r["converged"]
+        lat.set_links(inputs.unit_field(L))
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=100)
+        assert r["iters"] == 0 and r["converged"] and r["theta"] == 0.0 and r["F"] == pytest.approx(1.0, abs=1e-15)
