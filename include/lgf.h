@@ -36,6 +36,8 @@
 #ifndef LGF_H
 #define LGF_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -127,6 +129,19 @@ int lgf_get_gauge(lgf_ctx* ctx, double* G_out, int on_device);
  * number of pairs.  The device keeps the most recent 65536 pairs.
  */
 int lgf_get_history(lgf_ctx* ctx, double* theta_F, int n_max, int* written);
+
+/*
+ * Snapshots of the stored links in the context's own layout (no conversion, no
+ * check), for callers that return to earlier states many times, such as the
+ * checkpointed derivative through K steps (the paper has no counterpart).
+ * lgf_links_state_bytes: size of a snapshot.  lgf_save_links: copy the stored
+ * links to dst (device memory of that size).  lgf_load_links: store a snapshot
+ * that lgf_save_links wrote from a context of the same extents and flags, and
+ * reset G to 1.  Both block until the copy is done.
+ */
+size_t lgf_links_state_bytes(const lgf_ctx* ctx);
+int lgf_save_links(lgf_ctx* ctx, void* dst);
+int lgf_load_links(lgf_ctx* ctx, const void* src);
 
 /* lgf_stats: phase split of the last lgf_fix (iterations in the FP32 phase). */
 int lgf_get_stats(lgf_ctx* ctx, int* iters_fp32, int* iters_fp64);

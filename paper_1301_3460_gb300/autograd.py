@@ -16,18 +16,22 @@ from . import lgf
 
 
 class GaugeFixUnroll(torch.autograd.Function):
+    """Checkpoints and the states replayed in the backward are snapshots of the
+    library's own link layout (save_links / load_links): device-to-device copies,
+    without the conversion and SU(3) check of set_links."""
+
     @staticmethod
     def forward(ctx, U0, lat, K: int, alpha: float, every: int):
         U0 = U0.detach().contiguous()
         lat.set_links(U0)
-        ckpts = [U0]
+        ckpts = [lat.save_links()]
         done = 0
         while done < K:
             n = min(every, K - done)
             lat.fix(alpha, 0.0, n)
             done += n
             if done < K:
-                ckpts.append(lat.get_links(device=U0.device))
+                ckpts.append(lat.save_links())
         UK = lat.get_links(device=U0.device)
         ctx.lat, ctx.K, ctx.alpha, ctx.every, ctx.ckpts = lat, K, alpha, every, ckpts
         return UK
@@ -40,12 +44,12 @@ class GaugeFixUnroll(torch.autograd.Function):
         for si in reversed(range(nseg)):
             a, b = si * every, min(K, (si + 1) * every)
             states = [ctx.ckpts[si]]
-            lat.set_links(states[0])
+            lat.load_links(states[0])
             for _ in range(b - a - 1):
                 lat.fix(alpha, 0.0, 1)
-                states.append(lat.get_links(device=g.device))
+                states.append(lat.save_links())
             for k in reversed(range(b - a)):
-                lat.set_links(states[k])
+                lat.load_links(states[k])
                 g = lat.step_bwd(g, alpha)
         return g, None, None, None, None
 

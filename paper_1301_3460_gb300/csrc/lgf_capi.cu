@@ -909,6 +909,31 @@ int lgf_get_history(lgf_ctx* c, double* theta_F, int n_max, int* written)
     return LGF_OK;
 }
 
+size_t lgf_links_state_bytes(const lgf_ctx* c)
+{
+    return c ? (size_t)4 * c->lat.ne * c->V * sizeof(double2) : 0;
+}
+
+int lgf_save_links(lgf_ctx* c, void* dst)
+{
+    if (!c || !dst) return LGF_ERR_ARG;
+    if (!c->have_links) return LGF_ERR_STATE;
+    CK(cudaMemcpyAsync(dst, c->U64, lgf_links_state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LGF_OK;
+}
+
+int lgf_load_links(lgf_ctx* c, const void* src)
+{
+    if (!c || !src) return LGF_ERR_ARG;
+    CK(cudaMemcpyAsync(c->U64, src, lgf_links_state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_links = true;
+    return LGF_OK;
+}
+
 int lgf_get_stats(lgf_ctx* c, int* iters_fp32, int* iters_fp64)
 {
     if (!c) return LGF_ERR_ARG;

@@ -93,6 +93,9 @@ def load(build_if_missing: bool = True):
             "lgf_gluon_pmin": ([P, DP, DP], I),
             "lgf_gluon_pmin_bwd": ([P, D, P], I),
             "lgf_set_unit_links": ([P], I),
+            "lgf_links_state_bytes": ([P], ctypes.c_size_t),
+            "lgf_save_links": ([P, P], I),
+            "lgf_load_links": ([P, P], I),
             "lgf_wilson_sweeps": ([P, D, ctypes.c_ulonglong, I, I, I], I),
             "lgf_plaquette": ([P, DP], I),
             "lgf_batch_create": ([I, ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
@@ -450,3 +453,27 @@ def _plaquette(self) -> float:
 Lattice.set_unit_links = _set_unit_links
 Lattice.wilson_sweeps = _wilson_sweeps
 Lattice.plaquette = _plaquette
+
+
+def _save_links(self, out=None):
+    """Snapshot of the stored links in the library's layout: a uint8 CUDA tensor
+    (reused when `out` is given)."""
+    import torch
+
+    n = int(self._lib.lgf_links_state_bytes(self._h))
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    assert out.is_cuda and out.numel() == n and out.is_contiguous()
+    _check(self._lib.lgf_save_links(self._h, ctypes.c_void_p(out.data_ptr())), "lgf_save_links")
+    return out
+
+
+def _load_links(self, snap):
+    """Store a snapshot made by save_links of a lattice with the same extents and flags."""
+    n = int(self._lib.lgf_links_state_bytes(self._h))
+    assert snap.is_cuda and snap.numel() * snap.element_size() == n and snap.is_contiguous()
+    _check(self._lib.lgf_load_links(self._h, ctypes.c_void_p(snap.data_ptr())), "lgf_load_links")
+
+
+Lattice.save_links = _save_links
+Lattice.load_links = _load_links

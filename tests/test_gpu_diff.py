@@ -143,3 +143,24 @@ def test_step_fwd_matches_oracle(L):
     assert np.max(np.abs(out.cpu().numpy() - ref["U"])) < 1e-13
     ref2 = orc.fix(L, ref["U"], alpha=0.08, tol=0.0, max_iter=1)
     assert np.max(np.abs(again.cpu().numpy() - ref2["U"])) < 1e-13
+
+
+def test_link_snapshots_round_trip():
+    """save_links / load_links (the checkpoints of the unrolled derivative)
+    restore the stored links exactly, also into another lattice of the same
+    extents and flags, and reset G."""
+    L = (6, 4, 8, 4)
+    U = inputs.rough_gauge_field(L, 0.4, 31)
+    with lgf.Lattice(L) as a, lgf.Lattice(L) as b:
+        a.set_links(U)
+        snap = a.save_links()
+        before = a.get_links()
+        a.fix(0.08, 0.0, 3)
+        assert np.max(np.abs(a.get_links() - before)) > 1e-3
+        a.load_links(snap)
+        assert np.array_equal(a.get_links(), before)
+        assert np.array_equal(a.get_gauge(), inputs.unit_field(L)[0])
+        b.load_links(snap)
+        assert np.array_equal(b.get_links(), before)
+        r1, r2 = a.fix(0.08, 0.0, 2), b.fix(0.08, 0.0, 2)
+        assert np.array_equal(a.get_links(), b.get_links()) and r1["F"] == r2["F"]
