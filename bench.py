@@ -33,7 +33,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SD iters/s & time-to-theta<1e-15, 32^4 SU(3), FP64 vs mixed; % of HBM peak"
-FP64_PEAK_GFLOPS = 1250.0  # GB300 dense FP64 (nominal, 152 SMs); the probe measured 1190
+# GB300 dense FP64 from unit counts and clocks: 152 SMs x 2 FP64 FMAs per cycle per SM
+# (1.25 TFLOP/s nominal at the 2070 MHz maximum SM clock) x 2 flops x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 EPS = (0.15, 0.3, 0.5)
 SEEDS = (3201, 3202, 3203)
 
@@ -523,7 +525,8 @@ def run_ours(args, dims):
     traffic = traffic_record(kern, dims, 64)
     roof = {"bound": "alu", "kernel": kern, "achieved": flops / sec / 1e9, "peak": FP64_PEAK_GFLOPS,
             "unit": "GFLOP/s", "frac": flops / sec / 1e9 / FP64_PEAK_GFLOPS, "traffic": traffic,
-            "peak_source": "GB300 nominal dense FP64 (recipe table); measured FMA probe 1190 GFLOP/s",
+            "peak_source": "GB300 FP64: 152 SMs x 4 flops/cycle x 2.07 GHz (1.25 TFLOP/s nominal); an FMA probe "
+                           "measured 1190 GFLOP/s",
             "hbm_achieved_gbs": byts / sec / 1e9}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -716,7 +719,8 @@ def run_wilson(args, dims):
     hb = kinds["heatbath"]
     roof = {"bound": "alu", "kernel": "k_wilson (heat bath)", "achieved": hb["gflops"], "peak": FP64_PEAK_GFLOPS,
             "unit": "GFLOP/s", "frac": hb["gflops"] / FP64_PEAK_GFLOPS, "traffic": None,
-            "peak_source": "GB300 nominal dense FP64; flops per link exclude the sampler's transcendental functions"}
+            "peak_source": "GB300 FP64: 152 SMs x 4 flops/cycle x 2.07 GHz; flops per link exclude the sampler's "
+                           "transcendental functions"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle as orc
