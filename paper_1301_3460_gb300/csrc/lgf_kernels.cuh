@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, con
     const int s0 = plane * P;
     const int z = plane % d.L[2], t = plane / d.L[2];
     double th = 0.0, fsum = 0.0;
+#pragma unroll 4
     for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
         const int s = s0 + xy;
         const int x = xy % d.L[0], y = xy / d.L[0];
@@ -278,6 +279,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
     const int n = XW * Lz * Lt;
     const int LzXW = Lz * XW;
     // value i = xi + XW (z + Lz t) of the pencil sits at t RS + (i mod Lz XW) in the tile
+#pragma unroll 4
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int zt = i / XW, xi = i - zt * XW;
         const int t = i / LzXW;
@@ -293,6 +295,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t
     // multipliers (site-indexed by momentum) when there is one, else computed
     if (mult != nullptr) {
         const T* mrow = mult + x0 + d.L[0] * y;
+#pragma unroll 4
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int zt = i / XW, xi = i - zt * XW;
             const int o = i + (i / LzXW) * (RS - LzXW);
@@ -400,6 +403,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_xyinv_g(Lat d, const XyFft F, c
     if (ld_flag(&ctl->phase_done)) return;
     const int P = d.P, V = d.V;
     const int s0 = blockIdx.x * P;
+#pragma unroll 4
     for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
         const int f = i / P, xy = i - f * P;
         sm[i] = Fd[(size_t)f * V + s0 + xy];
