@@ -451,6 +451,17 @@ def run_ours(args, dims):
             msw = e0.elapsed_time(e1) / args.steps
             gf = roofline.WILSON_FLOPS_PER_LINK * 4 * V / msw / 1e6
             wilson[lab] = {"ms_per_sweep": msw, "gflops": gf, "frac_fp64_peak": gf / FP64_PEAK_GFLOPS}
+        # the FP32-staple generator
+        lw.set_generator_precision(32)
+        for lab, nhb, nor in (("heatbath_fp32", 1, 0), ("overrelax_fp32", 0, 1)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.steps):
+                lw.wilson_sweeps(6.0, 7, first_sweep=100 + k, n_heatbath=nhb, n_overrelax=nor)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wilson[lab] = {"ms_per_sweep": e0.elapsed_time(e1) / args.steps}
+        lw.set_generator_precision(64)
         wilson["plaquette"] = lw.plaquette()
         # generate -> fix on the device: Wilson-action configurations at three couplings
         # (cold start, 40 x (heat bath + 4 overrelaxation)), then FP64 gauge fixing
@@ -714,6 +725,16 @@ def run_wilson(args, dims):
         msw = f0.elapsed_time(f1) / 3
         gf = roofline.WILSON_FLOPS_PER_LINK * 4 * V / msw / 1e6
         kinds[lab] = {"ms_per_sweep": msw, "ms_per_launch": msw / 8, "gflops": gf}
+    lat.set_generator_precision(32)
+    for lab, nhb, nor in (("heatbath_fp32", 1, 0), ("overrelax_fp32", 0, 1)):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(3):
+            lat.wilson_sweeps(args.beta, seed, first_sweep=args.warmup + args.steps + 3 + k, n_heatbath=nhb,
+                              n_overrelax=nor)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        kinds[lab] = {"ms_per_sweep": f0.elapsed_time(f1) / 3}
     plaq = lat.plaquette()
     lat.close()
     hb = kinds["heatbath"]

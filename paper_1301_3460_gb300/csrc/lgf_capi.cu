@@ -122,6 +122,7 @@ struct lgf_ctx {
     double2* gl_At = nullptr;  // [16][9]
     double* gl_D = nullptr;    // [5]
     double* wil_part = nullptr;  // plaquette partial sums, then the result
+    int gen_precision = 64;      // arithmetic of the configuration generator's staples and draws
 };
 
 namespace {
@@ -1327,12 +1328,19 @@ int lgf_wilson_sweeps(lgf_ctx* c, double beta, unsigned long long seed, int firs
         for (int mode = n_heatbath > 0 ? 0 : 1; mode < 1 + n_overrelax; mode++)
             for (int mu = 0; mu < 4; mu++)
                 for (int par = 0; par < 2; par++)
-                    launch_wilson(c->stream, c->lat, c->U64, mu, par, mode > 0, beta, seed, sweep);
+                    launch_wilson(c->stream, c->lat, c->U64, mu, par, mode > 0, beta, seed, sweep, c->gen_precision);
         CK(cudaGetLastError());
     }
     if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
+    return LGF_OK;
+}
+
+int lgf_set_generator_precision(lgf_ctx* c, int bits)
+{
+    if (!c || (bits != 64 && bits != 32)) return LGF_ERR_ARG;
+    c->gen_precision = bits;
     return LGF_OK;
 }
 

@@ -76,7 +76,7 @@ void launch_gluon_bwd(cudaStream_t s, const Lat& d, const double2* U, const doub
 // Wilson-action heat bath / overrelaxation of one (mu, parity) class of links,
 // and the mean plaquette (lgf_wilson.cu)
 void launch_wilson(cudaStream_t s, const Lat& d, double2* U, int mu, int parity, int overrelax, double beta,
-                   unsigned long long seed, unsigned int sweep);
+                   unsigned long long seed, unsigned int sweep, int precision);
 void launch_unit_links(cudaStream_t s, const Lat& d, double2* U);
 int plaquette_blocks(int V);
 void launch_plaquette(cudaStream_t s, const Lat& d, const double2* U, double* part, double* out);

@@ -45,34 +45,45 @@ constexpr int kWilsonThreads = 128;
 constexpr int kPlaqThreads = 256;
 constexpr int kPlaqBlocks = 1216;  // 8 per SM on 152 SMs; grid-stride beyond
 
-__device__ __forceinline__ void load3(const double2* __restrict__ U, int V, int ne, int mu, int s, C* m)
+// matrix helpers for T = double (the FP64 generator) and T = float (the staples
+// of the FP32 one); links are FP64 in memory in both cases
+
+template <typename T> __device__ __forceinline__ cx<T> ldl(const double2* p)
+{
+    const double2 v = __ldg(p);
+    return mk<T>((T)v.x, (T)v.y);
+}
+
+template <typename T>
+__device__ __forceinline__ void load3(const double2* __restrict__ U, int V, int ne, int mu, int s, cx<T>* m)
 {
 #pragma unroll
-    for (int e = 0; e < 6; e++) m[e] = ld<double>(U + (size_t)(mu * ne + e) * V + s);
+    for (int e = 0; e < 6; e++) m[e] = ldl<T>(U + (size_t)(mu * ne + e) * V + s);
     if (ne == 9) {
 #pragma unroll
-        for (int e = 6; e < 9; e++) m[e] = ld<double>(U + (size_t)(mu * 9 + e) * V + s);
+        for (int e = 6; e < 9; e++) m[e] = ldl<T>(U + (size_t)(mu * 9 + e) * V + s);
     } else {
         complete_row2(m, m + 6);
     }
 }
 
 // rows 0,1 of a link (all that a product whose row 2 is rebuilt needs)
-__device__ __forceinline__ void load2(const double2* __restrict__ U, int V, int ne, int mu, int s, C* m)
+template <typename T>
+__device__ __forceinline__ void load2(const double2* __restrict__ U, int V, int ne, int mu, int s, cx<T>* m)
 {
 #pragma unroll
-    for (int e = 0; e < 6; e++) m[e] = ld<double>(U + (size_t)(mu * ne + e) * V + s);
+    for (int e = 0; e < 6; e++) m[e] = ldl<T>(U + (size_t)(mu * ne + e) * V + s);
 }
 
 // c = a b for a, b in SU(3): rows 0,1 multiplied out, row 2 = conj(row0 x row1)
 // (a's row 2 is not read)
-__device__ __forceinline__ void mm_su3(const C* a, const C* b, C* c)
+template <typename T> __device__ __forceinline__ void mm_su3(const cx<T>* a, const cx<T>* b, cx<T>* c)
 {
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            C t = cmul(a[3 * i], b[j]);
+            cx<T> t = cmul(a[3 * i], b[j]);
             t = cmac(t, a[3 * i + 1], b[3 + j]);
             c[3 * i + j] = cmac(t, a[3 * i + 2], b[6 + j]);
         }
@@ -80,26 +91,26 @@ __device__ __forceinline__ void mm_su3(const C* a, const C* b, C* c)
 }
 
 // c = a b
-__device__ __forceinline__ void mm(const C* a, const C* b, C* c)
+template <typename T> __device__ __forceinline__ void mm(const cx<T>* a, const cx<T>* b, cx<T>* c)
 {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            C t = cmul(a[3 * i], b[j]);
+            cx<T> t = cmul(a[3 * i], b[j]);
             t = cmac(t, a[3 * i + 1], b[3 + j]);
             c[3 * i + j] = cmac(t, a[3 * i + 2], b[6 + j]);
         }
 }
 
 // acc += a b^dag
-__device__ __forceinline__ void mm_nd_acc(const C* a, const C* b, C* acc)
+template <typename T> __device__ __forceinline__ void mm_nd_acc(const cx<T>* a, const cx<T>* b, cx<T>* acc)
 {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            C t = acc[3 * i + j];
+            cx<T> t = acc[3 * i + j];
 #pragma unroll
             for (int k = 0; k < 3; k++) t = cmacc(t, a[3 * i + k], b[3 * j + k]);
             acc[3 * i + j] = t;
@@ -107,17 +118,46 @@ __device__ __forceinline__ void mm_nd_acc(const C* a, const C* b, C* acc)
 }
 
 // acc += a^dag b
-__device__ __forceinline__ void mm_dn_acc(const C* a, const C* b, C* acc)
+template <typename T> __device__ __forceinline__ void mm_dn_acc(const cx<T>* a, const cx<T>* b, cx<T>* acc)
 {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            C t = acc[3 * i + j];
+            cx<T> t = acc[3 * i + j];
 #pragma unroll
             for (int k = 0; k < 3; k++) t = cmacc(t, b[3 * k + j], a[3 * k + i]);
             acc[3 * i + j] = t;
         }
+}
+
+// staple sum A of link (mu, s) of parity c
+template <typename T>
+__device__ __forceinline__ void staple_sum(const Lat& d, const double2* __restrict__ U, int mu, int s, const int* c,
+                                           cx<T>* A)
+{
+    const int V = d.V, ne = d.ne;
+#pragma unroll
+    for (int e = 0; e < 9; e++) A[e] = mk<T>(0, 0);
+    const int sp = site_shift(d, s, c[mu], mu, +1);
+#pragma unroll
+    for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        const int snp = site_shift(d, s, c[nu], nu, +1);
+        const int snm = site_shift(d, s, c[nu], nu, -1);
+        const int spm = site_shift(d, sp, c[nu], nu, -1);  // x + mu - nu
+        cx<T> a[9], b[9], q[9];
+        load2<T>(U, V, ne, nu, s, a);
+        load3<T>(U, V, ne, mu, snp, b);
+        mm_su3<T>(a, b, q);             // U_nu(x) U_mu(x+nu)
+        load3<T>(U, V, ne, nu, sp, a);
+        mm_nd_acc<T>(a, q, A);          // + U_nu(x+mu) q^dag
+        load2<T>(U, V, ne, mu, snm, a);
+        load3<T>(U, V, ne, nu, spm, b);
+        mm_su3<T>(a, b, q);             // U_mu(x-nu) U_nu(x+mu-nu)
+        load3<T>(U, V, ne, nu, snm, a);
+        mm_dn_acc<T>(q, a, A);          // + q^dag U_nu(x-nu)
+    }
 }
 
 // ---------------------------------------------------------------- Philox4x32-10
@@ -191,12 +231,12 @@ __device__ __noinline__ void su2_draw(double b, uint32_t k0, uint32_t k1, uint32
 }
 
 // rows i, j of m <- R (rows i, j)
-template <int I, int J>
-__device__ __forceinline__ void rot_rows(C* m, C R00, C R01, C R10, C R11)
+template <int I, int J, typename T>
+__device__ __forceinline__ void rot_rows(cx<T>* m, cx<T> R00, cx<T> R01, cx<T> R10, cx<T> R11)
 {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const C mi = m[3 * I + c], mj = m[3 * J + c];
+        const cx<T> mi = m[3 * I + c], mj = m[3 * J + c];
         m[3 * I + c] = cmac(cmul(R00, mi), R01, mj);
         m[3 * J + c] = cmac(cmul(R10, mi), R11, mj);
     }
@@ -280,35 +320,143 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson(Lat d, double2* __res
     const int V = d.V, ne = d.ne;
 
     C A[9];
-#pragma unroll
-    for (int e = 0; e < 9; e++) A[e] = mk(0.0, 0.0);
-    const int sp = site_shift(d, s, c[mu], mu, +1);
-#pragma unroll
-    for (int nu = 0; nu < 4; nu++) {
-        if (nu == mu) continue;
-        const int snp = site_shift(d, s, c[nu], nu, +1);
-        const int snm = site_shift(d, s, c[nu], nu, -1);
-        const int spm = site_shift(d, sp, c[nu], nu, -1);  // x + mu - nu
-        C a[9], b[9], q[9];
-        load2(U, V, ne, nu, s, a);
-        load3(U, V, ne, mu, snp, b);
-        mm_su3(a, b, q);             // U_nu(x) U_mu(x+nu)
-        load3(U, V, ne, nu, sp, a);
-        mm_nd_acc(a, q, A);          // + U_nu(x+mu) q^dag
-        load2(U, V, ne, mu, snm, a);
-        load3(U, V, ne, nu, spm, b);
-        mm_su3(a, b, q);             // U_mu(x-nu) U_nu(x+mu-nu)
-        load3(U, V, ne, nu, snm, a);
-        mm_dn_acc(q, a, A);          // + q^dag U_nu(x-nu)
-    }
+    staple_sum<double>(d, U, mu, s, c, A);
     C u[9], w[9];
-    load3(U, V, ne, mu, s, u);
-    mm(u, A, w);
+    load3<double>(U, V, ne, mu, s, u);
+    mm<double>(u, A, w);
     const uint32_t link = (uint32_t)mu * (uint32_t)V + (uint32_t)s;
     const double beta23 = beta * (2.0 / 3.0);  // b = 2 beta k / 3
     subgroup<MODE, 0, 1>(u, w, beta23, k0, k1, link, sweep, 0);
     subgroup<MODE, 0, 2>(u, w, beta23, k0, k1, link, sweep, 1);
     subgroup<MODE, 1, 2>(u, w, beta23, k0, k1, link, sweep, 2);
+    reunit(u);
+#pragma unroll
+    for (int e = 0; e < 6; e++) st<double>(U + (size_t)(mu * ne + e) * V + s, u[e]);
+    if (ne == 9) {
+#pragma unroll
+        for (int e = 6; e < 9; e++) st<double>(U + (size_t)(mu * 9 + e) * V + s, u[e]);
+    }
+}
+
+// ---------------------------------------------------------------- FP32 staples
+
+// The same update with the staples, W and the SU(2) draws in FP32 (links stay
+// FP64 in memory: R is applied to the FP64 link and the link re-orthonormalised
+// in FP64, so it stays in SU(3) to FP64 rounding).  A Markov chain of its own:
+// the heat bath samples exp((beta/3) Re Tr(U A)) with A known to FP32 rounding,
+// and its uniforms take the top 24 bits of the same Philox words.
+
+__device__ __forceinline__ void draw4f(uint32_t k0, uint32_t k1, uint32_t link, uint32_t sweep, uint32_t n, float u[4])
+{
+    uint32_t c[4] = {link, sweep, n, 0u};
+    philox(c, k0, k1);
+#pragma unroll
+    for (int i = 0; i < 4; i++) u[i] = fmaf((float)(c[i] >> 8), 0x1p-24f, 0x1p-25f);
+}
+
+__device__ __noinline__ void su2_draw_f(float b, uint32_t k0, uint32_t k1, uint32_t link, uint32_t sweep, int sub,
+                                        float y[4])
+{
+    const bool kp = b >= 1.6f;
+    const float ib = b > 0 ? 1.0f / b : 0.0f;
+    const float e2b = kp ? 0.0f : expm1f(-2.0f * b);
+    for (int a = 0; a < 512; a++) {
+        float u[4];
+        draw4f(k0, k1, link, sweep, (uint32_t)(1024 * sub + 2 * a), u);
+        float y0;
+        bool ok;
+        if (kp) {
+            const float c = cospif(2.0f * u[1]);
+            const float lam2 = -(logf(u[0]) + c * c * logf(u[2])) * (0.5f * ib);
+            ok = u[3] * u[3] <= 1.0f - lam2;
+            y0 = 1.0f - 2.0f * lam2;
+        } else {
+            y0 = b > 0 ? 1.0f + log1pf((1.0f - u[0]) * e2b) * ib : 2.0f * u[0] - 1.0f;
+            ok = u[1] * u[1] <= 1.0f - y0 * y0;
+        }
+        if (ok) {
+            float v[4];
+            draw4f(k0, k1, link, sweep, (uint32_t)(1024 * sub + 2 * a + 1), v);
+            const float ct = 2.0f * v[0] - 1.0f;
+            const float st = sqrtf(fmaxf(1.0f - ct * ct, 0.0f));
+            float sp, cp;
+            sincospif(2.0f * v[1], &sp, &cp);
+            const float rr = sqrtf(fmaxf(1.0f - y0 * y0, 0.0f));
+            y[0] = y0;
+            y[1] = rr * st * cp;
+            y[2] = rr * st * sp;
+            y[3] = rr * ct;
+            return;
+        }
+    }
+    y[0] = 1.0f;
+    y[1] = y[2] = y[3] = 0.0f;
+}
+
+// rows i, j of the FP32 matrix w and of the FP64 link u <- R (rows i, j)
+template <int MODE, int I, int J>
+__device__ __forceinline__ void subgroup32(C* u, cx<float>* w, float beta23, uint32_t k0, uint32_t k1, uint32_t link,
+                                           uint32_t sweep, int sub)
+{
+    using F = cx<float>;
+    const F wii = w[3 * I + I], wjj = w[3 * J + J], wij = w[3 * I + J], wji = w[3 * J + I];
+    const F r = mk(0.5f * (wii.re + wjj.re), 0.5f * (wii.im - wjj.im));
+    const F s = mk(0.5f * (wij.re - wji.re), 0.5f * (wij.im + wji.im));
+    const float k2 = r.re * r.re + r.im * r.im + s.re * s.re + s.im * s.im;
+    if (!(k2 > 0)) return;
+    const float ik = rsqrtf(k2);
+    const F a = r * ik, b = s * ik;
+    F R00, R01, R10, R11;
+    if (MODE == 0) {
+        float y[4];
+        su2_draw_f(beta23 * (k2 * ik), k0, k1, link, sweep, sub, y);
+        const F Y00 = mk(y[0], y[3]), Y01 = mk(y[2], y[1]), Y10 = mk(-y[2], y[1]), Y11 = mk(y[0], -y[3]);
+        const F nb = mk(-b.re, -b.im);
+        R00 = cmac(cmul(Y00, conjg(a)), Y01, conjg(b));
+        R01 = cmac(cmul(Y00, nb), Y01, a);
+        R10 = cmac(cmul(Y10, conjg(a)), Y11, conjg(b));
+        R11 = cmac(cmul(Y10, nb), Y11, a);
+    } else {
+        const F D00 = conjg(a), D01 = mk(-b.re, -b.im), D10 = conjg(b), D11 = a;
+        R00 = cmac(cmul(D00, D00), D01, D10);
+        R01 = cmac(cmul(D00, D01), D01, D11);
+        R10 = cmac(cmul(D10, D00), D11, D10);
+        R11 = cmac(cmul(D10, D01), D11, D11);
+    }
+    rot_rows<I, J>(w, R00, R01, R10, R11);
+    rot_rows<I, J>(u, mk((double)R00.re, (double)R00.im), mk((double)R01.re, (double)R01.im),
+                   mk((double)R10.re, (double)R10.im), mk((double)R11.re, (double)R11.im));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __restrict__ U, int mu, int parity,
+                                                             float beta, uint32_t k0, uint32_t k1, uint32_t sweep)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= (d.V >> 1)) return;
+    const int hx = d.L[0] >> 1;
+    int c[4];
+    int r = h / hx;
+    const int xh = h - r * hx;
+    c[1] = r % d.L[1];
+    r /= d.L[1];
+    c[2] = r % d.L[2];
+    c[3] = r / d.L[2];
+    c[0] = 2 * xh + ((parity + c[1] + c[2] + c[3]) & 1);
+    const int s = c[0] + d.stride[1] * c[1] + d.stride[2] * c[2] + d.stride[3] * c[3];
+    const int V = d.V, ne = d.ne;
+    cx<float> A[9], uf[9], w[9];
+    staple_sum<float>(d, U, mu, s, c, A);
+    C u[9];
+    load3<double>(U, V, ne, mu, s, u);
+#pragma unroll
+    for (int e = 0; e < 9; e++) uf[e] = mk((float)u[e].re, (float)u[e].im);
+    mm<float>(uf, A, w);
+    const uint32_t link = (uint32_t)mu * (uint32_t)V + (uint32_t)s;
+    const float beta23 = beta * (2.0f / 3.0f);
+    subgroup32<MODE, 0, 1>(u, w, beta23, k0, k1, link, sweep, 0);
+    subgroup32<MODE, 0, 2>(u, w, beta23, k0, k1, link, sweep, 1);
+    subgroup32<MODE, 1, 2>(u, w, beta23, k0, k1, link, sweep, 2);
     reunit(u);
 #pragma unroll
     for (int e = 0; e < 6; e++) st<double>(U + (size_t)(mu * ne + e) * V + s, u[e]);
@@ -333,12 +481,12 @@ __global__ void __launch_bounds__(kPlaqThreads) k_plaq_partial(Lat d, const doub
             for (int nu = mu + 1; nu < 4; nu++) {
                 const int sn = site_shift(d, s, c[nu], nu, +1);
                 C a[9], b[9], p1[9], p2[9];
-                load3(U, d.V, d.ne, mu, s, a);
-                load3(U, d.V, d.ne, nu, sp, b);
-                mm(a, b, p1);
-                load3(U, d.V, d.ne, nu, s, a);
-                load3(U, d.V, d.ne, mu, sn, b);
-                mm(a, b, p2);
+                load3<double>(U, d.V, d.ne, mu, s, a);
+                load3<double>(U, d.V, d.ne, nu, sp, b);
+                mm<double>(a, b, p1);
+                load3<double>(U, d.V, d.ne, nu, s, a);
+                load3<double>(U, d.V, d.ne, mu, sn, b);
+                mm<double>(a, b, p2);
 #pragma unroll
                 for (int e = 0; e < 9; e++) acc += p1[e].re * p2[e].re + p1[e].im * p2[e].im;
             }
@@ -394,14 +542,20 @@ int plaquette_blocks(int V)
 }
 
 void launch_wilson(cudaStream_t s, const Lat& d, double2* U, int mu, int parity, int overrelax, double beta,
-                   unsigned long long seed, unsigned int sweep)
+                   unsigned long long seed, unsigned int sweep, int precision)
 {
     const unsigned nb = (unsigned)((d.V / 2 + kWilsonThreads - 1) / kWilsonThreads);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    if (overrelax)
+    if (precision == 32) {
+        if (overrelax)
+            k_wilson32<1><<<nb, kWilsonThreads, 0, s>>>(d, U, mu, parity, (float)beta, k0, k1, sweep);
+        else
+            k_wilson32<0><<<nb, kWilsonThreads, 0, s>>>(d, U, mu, parity, (float)beta, k0, k1, sweep);
+    } else if (overrelax) {
         k_wilson<1><<<nb, kWilsonThreads, 0, s>>>(d, U, mu, parity, beta, k0, k1, sweep);
-    else
+    } else {
         k_wilson<0><<<nb, kWilsonThreads, 0, s>>>(d, U, mu, parity, beta, k0, k1, sweep);
+    }
 }
 
 void launch_plaquette(cudaStream_t s, const Lat& d, const double2* U, double* part, double* out)

@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
             "lgf_load_links": ([P, P], I),
             "lgf_wilson_sweeps": ([P, D, ctypes.c_ulonglong, I, I, I], I),
             "lgf_plaquette": ([P, DP], I),
+            "lgf_set_generator_precision": ([P, I], I),
             "lgf_batch_create": ([I, ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
             "lgf_batch_set_stream": ([P, P], I),
             "lgf_batch_set_links": ([P, I, P, I], I),
@@ -450,6 +451,12 @@ def _plaquette(self) -> float:
     return P.value
 
 
+def _set_generator_precision(self, bits: int):
+    """64 (default) or 32: arithmetic of the Wilson generator's staples and draws."""
+    _check(self._lib.lgf_set_generator_precision(self._h, int(bits)), "lgf_set_generator_precision")
+
+
+Lattice.set_generator_precision = _set_generator_precision
 Lattice.set_unit_links = _set_unit_links
 Lattice.wilson_sweeps = _wilson_sweeps
 Lattice.plaquette = _plaquette

@@ -165,3 +165,36 @@ def test_beta6_plaquette():
             lat.wilson_sweeps(6.0, 2024, first_sweep=150 + n, n_heatbath=1, n_overrelax=4)
             ps.append(lat.plaquette())
     assert abs(np.mean(ps) - 0.5937) < 0.001
+
+
+def test_fp32_generator():
+    """The FP32-staple generator: links stay in SU(3) to FP64 rounding,
+    overrelaxation keeps the action to FP32 rounding of the staples, and the
+    chain has the Wilson action's plaquette at strong coupling (beta/18 +
+    beta^2/216) and at beta = 6.0 (0.5937 on 16^4)."""
+    L = (6, 6, 4, 8)
+    U = inputs.rough_gauge_field(L, 0.5, 41)
+    with lgf.Lattice(L, track_gauge=False) as lat:
+        lat.set_generator_precision(32)
+        lat.set_links(U)
+        p0 = lat.plaquette()
+        lat.wilson_sweeps(6.0, 3, n_heatbath=0, n_overrelax=2)
+        assert abs(lat.plaquette() - p0) < 1e-5
+        Ug = lat.get_links()
+        assert np.max(np.abs(Ug - U)) > 0.1
+        lat.wilson_sweeps(6.0, 3, n_heatbath=3, n_overrelax=1)
+        M = lat.get_links().reshape(-1, 3, 3)
+        assert np.abs(M @ np.conj(np.transpose(M, (0, 2, 1))) - np.eye(3)).max() < 1e-13
+        with pytest.raises(lgf.LgfError):
+            lat.set_generator_precision(16)
+    for L, beta, n_therm, n_meas, want, tol in (((8, 8, 8, 8), 1.0, 20, 100, 1.0 / 18 + 1.0 / 216, 0.0015),
+                                                  ((16, 16, 16, 16), 6.0, 150, 40, 0.5937, 0.001)):
+        with lgf.Lattice(L, track_gauge=False) as lat:
+            lat.set_generator_precision(32)
+            lat.set_unit_links()
+            lat.wilson_sweeps(beta, 99, first_sweep=0, n_heatbath=n_therm, n_overrelax=4 if beta > 3 else 2)
+            ps = []
+            for n in range(n_meas):
+                lat.wilson_sweeps(beta, 99, first_sweep=n_therm + n, n_heatbath=1, n_overrelax=4 if beta > 3 else 2)
+                ps.append(lat.plaquette())
+        assert abs(np.mean(ps) - want) < tol
