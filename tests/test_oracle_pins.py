@@ -379,3 +379,33 @@ def test_plain_sd_converges_and_keeps_invariants():
     assert abs(orc.plaquette(L, r["U"]) - orc.plaquette(L, U0)) < 1e-13
     ra = orc.fix(L, U0, alpha=0.08, tol=1e-15, max_iter=20000, accelerate=True)
     assert ra["iters"] < r["iters"]
+
+
+def test_delta_is_the_gradient_of_F():
+    """Delta is the gradient of the functional (the steepest-descent direction):
+    rotating one site by g = exp(t X), X traceless anti-Hermitian, changes
+    F_U[g] = 1/(12 V) sum Re Tr[g(x) U_mu(x) g^dag(x+mu)] at the rate
+    dF/dt = -Tr[X Delta(x0)] / (24 V).  Central differences of the oracle's F
+    against that formula pin Delta's sign, normalisation and site convention."""
+    from scipy.linalg import expm
+
+    L = (4, 4, 6, 4)
+    V = int(np.prod(L))
+    U = inputs.rough_gauge_field(L, 0.4, 77)
+    D, _, F0 = orc.delta(L, U)
+    rng = np.random.default_rng(5)
+    for x0 in (0, 17, V - 1):
+        X = 1j * inputs.random_su3_algebra(rng, (1,))[0]  # traceless anti-Hermitian
+        assert abs(np.trace(X)) < 1e-14 and np.abs(X + dag(X)).max() < 1e-14
+        h = 1e-5
+        vals = []
+        for t in (h, -h):
+            G = np.zeros((V, 3, 3), complex)
+            G[:] = np.eye(3)
+            G[x0] = expm(t * X)
+            _, _, F = orc.delta(L, orc.gauge_transform(L, U, G))
+            vals.append(F)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        want = -np.real(np.trace(X @ D[x0])) / (24 * V)
+        assert abs(fd - want) < 1e-9 * max(1.0, abs(want)) + 1e-12
+        assert abs(want) > 1e-6
