@@ -123,6 +123,7 @@ struct lgf_ctx {
     double* gl_D = nullptr;    // [5]
     double* wil_part = nullptr;  // plaquette partial sums, then the result
     int gen_precision = 64;      // arithmetic of the configuration generator's staples and draws
+    float2* gen32 = nullptr;     // [4][6][V]: FP32 copy of the links for the FP32 generator's staples
 };
 
 namespace {
@@ -443,7 +444,7 @@ void free_all(lgf_ctx* c)
     if (c->exec) cudaGraphExecDestroy(c->exec);
     void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
                     c->hist, c->err, c->stage, c->tables, c->mult, c->AH64, c->Fs64, c->AH32, c->Fs32, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
-                    c->gl_part, c->gl_At, c->gl_D, c->wil_part};
+                    c->gl_part, c->gl_At, c->gl_D, c->wil_part, c->gen32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_ctl) cudaFreeHost(c->host_ctl);
@@ -1321,6 +1322,10 @@ int lgf_wilson_sweeps(lgf_ctx* c, double beta, unsigned long long seed, int firs
     for (int mu = 0; mu < 4; mu++)
         if (c->L[mu] % 2) return LGF_ERR_UNSUPPORTED_DIMS;  // the checkerboard needs even extents
     if ((long long)first_sweep + n_heatbath > 0xffffffffLL) return LGF_ERR_ARG;
+    if (c->gen_precision == 32) {
+        if (!c->gen32) CKR(alloc((void**)&c->gen32, (size_t)24 * c->V * sizeof(float2)));
+        launch_links_to_fp32(c->stream, c->lat, c->U64, c->gen32);
+    }
     // n_heatbath = 0: overrelaxation sweeps only
     const int rounds = n_heatbath > 0 ? n_heatbath : 1;
     for (int i = 0; i < rounds; i++) {
@@ -1328,7 +1333,8 @@ int lgf_wilson_sweeps(lgf_ctx* c, double beta, unsigned long long seed, int firs
         for (int mode = n_heatbath > 0 ? 0 : 1; mode < 1 + n_overrelax; mode++)
             for (int mu = 0; mu < 4; mu++)
                 for (int par = 0; par < 2; par++)
-                    launch_wilson(c->stream, c->lat, c->U64, mu, par, mode > 0, beta, seed, sweep, c->gen_precision);
+                    launch_wilson(c->stream, c->lat, c->U64, c->gen32, mu, par, mode > 0, beta, seed, sweep,
+                                  c->gen_precision);
         CK(cudaGetLastError());
     }
     if (c->track) launch_identity_rows64(c->stream, c->V, c->G64);

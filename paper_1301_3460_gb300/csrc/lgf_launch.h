@@ -75,8 +75,9 @@ void launch_gluon_bwd(cudaStream_t s, const Lat& d, const double2* U, const doub
                       double2* Gout);
 // Wilson-action heat bath / overrelaxation of one (mu, parity) class of links,
 // and the mean plaquette (lgf_wilson.cu)
-void launch_wilson(cudaStream_t s, const Lat& d, double2* U, int mu, int parity, int overrelax, double beta,
-                   unsigned long long seed, unsigned int sweep, int precision);
+void launch_wilson(cudaStream_t s, const Lat& d, double2* U, float2* U32, int mu, int parity, int overrelax,
+                   double beta, unsigned long long seed, unsigned int sweep, int precision);
+void launch_links_to_fp32(cudaStream_t s, const Lat& d, const double2* U, float2* U32);
 void launch_unit_links(cudaStream_t s, const Lat& d, double2* U);
 int plaquette_blocks(int V);
 void launch_plaquette(cudaStream_t s, const Lat& d, const double2* U, double* part, double* out);

@@ -53,9 +53,14 @@ template <typename T> __device__ __forceinline__ cx<T> ldl(const double2* p)
     const double2 v = __ldg(p);
     return mk<T>((T)v.x, (T)v.y);
 }
+template <typename T> __device__ __forceinline__ cx<T> ldl(const float2* p)
+{
+    const float2 v = __ldg(p);
+    return mk<T>((T)v.x, (T)v.y);
+}
 
-template <typename T>
-__device__ __forceinline__ void load3(const double2* __restrict__ U, int V, int ne, int mu, int s, cx<T>* m)
+template <typename T, typename S>
+__device__ __forceinline__ void load3(const S* __restrict__ U, int V, int ne, int mu, int s, cx<T>* m)
 {
 #pragma unroll
     for (int e = 0; e < 6; e++) m[e] = ldl<T>(U + (size_t)(mu * ne + e) * V + s);
@@ -68,8 +73,8 @@ __device__ __forceinline__ void load3(const double2* __restrict__ U, int V, int 
 }
 
 // rows 0,1 of a link (all that a product whose row 2 is rebuilt needs)
-template <typename T>
-__device__ __forceinline__ void load2(const double2* __restrict__ U, int V, int ne, int mu, int s, cx<T>* m)
+template <typename T, typename S>
+__device__ __forceinline__ void load2(const S* __restrict__ U, int V, int ne, int mu, int s, cx<T>* m)
 {
 #pragma unroll
     for (int e = 0; e < 6; e++) m[e] = ldl<T>(U + (size_t)(mu * ne + e) * V + s);
@@ -132,8 +137,8 @@ template <typename T> __device__ __forceinline__ void mm_dn_acc(const cx<T>* a, 
 }
 
 // staple sum A of link (mu, s) of parity c
-template <typename T>
-__device__ __forceinline__ void staple_sum(const Lat& d, const double2* __restrict__ U, int mu, int s, const int* c,
+template <typename T, typename S>
+__device__ __forceinline__ void staple_sum(const Lat& d, const S* __restrict__ U, int mu, int s, const int* c,
                                            cx<T>* A)
 {
     const int V = d.V, ne = d.ne;
@@ -428,9 +433,12 @@ __device__ __forceinline__ void subgroup32(C* u, cx<float>* w, float beta23, uin
                    mk((double)R10.re, (double)R10.im), mk((double)R11.re, (double)R11.im));
 }
 
+// U32: an FP32 copy of rows 0,1 of every link ([mu][6][V]), read for the staples
+// and kept up to date with the links this launch writes.
 template <int MODE>
-__global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __restrict__ U, int mu, int parity,
-                                                             float beta, uint32_t k0, uint32_t k1, uint32_t sweep)
+__global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __restrict__ U, float2* __restrict__ U32,
+                                                             int mu, int parity, float beta, uint32_t k0, uint32_t k1,
+                                                             uint32_t sweep)
 {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= (d.V >> 1)) return;
@@ -446,7 +454,11 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __r
     const int s = c[0] + d.stride[1] * c[1] + d.stride[2] * c[2] + d.stride[3] * c[3];
     const int V = d.V, ne = d.ne;
     cx<float> A[9], uf[9], w[9];
-    staple_sum<float>(d, U, mu, s, c, A);
+    {
+        Lat d32 = d;
+        d32.ne = 6;
+        staple_sum<float>(d32, U32, mu, s, c, A);
+    }
     C u[9];
     load3<double>(U, V, ne, mu, s, u);
 #pragma unroll
@@ -459,11 +471,27 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __r
     subgroup32<MODE, 1, 2>(u, w, beta23, k0, k1, link, sweep, 2);
     reunit(u);
 #pragma unroll
-    for (int e = 0; e < 6; e++) st<double>(U + (size_t)(mu * ne + e) * V + s, u[e]);
+    for (int e = 0; e < 6; e++) {
+        st<double>(U + (size_t)(mu * ne + e) * V + s, u[e]);
+        U32[(size_t)(mu * 6 + e) * V + s] = make_float2((float)u[e].re, (float)u[e].im);
+    }
     if (ne == 9) {
 #pragma unroll
         for (int e = 6; e < 9; e++) st<double>(U + (size_t)(mu * 9 + e) * V + s, u[e]);
     }
+}
+
+// the FP32 copy of rows 0,1 of every link
+__global__ void k_links_to_fp32(Lat d, const double2* __restrict__ U, float2* __restrict__ U32)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.V) return;
+    for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+        for (int e = 0; e < 6; e++) {
+            const double2 v = U[(size_t)(mu * d.ne + e) * d.V + s];
+            U32[(size_t)(mu * 6 + e) * d.V + s] = make_float2((float)v.x, (float)v.y);
+        }
 }
 
 // ---------------------------------------------------------------- plaquette
@@ -541,16 +569,21 @@ int plaquette_blocks(int V)
     return nb < kPlaqBlocks ? nb : kPlaqBlocks;
 }
 
-void launch_wilson(cudaStream_t s, const Lat& d, double2* U, int mu, int parity, int overrelax, double beta,
-                   unsigned long long seed, unsigned int sweep, int precision)
+void launch_links_to_fp32(cudaStream_t s, const Lat& d, const double2* U, float2* U32)
+{
+    k_links_to_fp32<<<(unsigned)((d.V + 255) / 256), 256, 0, s>>>(d, U, U32);
+}
+
+void launch_wilson(cudaStream_t s, const Lat& d, double2* U, float2* U32, int mu, int parity, int overrelax,
+                   double beta, unsigned long long seed, unsigned int sweep, int precision)
 {
     const unsigned nb = (unsigned)((d.V / 2 + kWilsonThreads - 1) / kWilsonThreads);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     if (precision == 32) {
         if (overrelax)
-            k_wilson32<1><<<nb, kWilsonThreads, 0, s>>>(d, U, mu, parity, (float)beta, k0, k1, sweep);
+            k_wilson32<1><<<nb, kWilsonThreads, 0, s>>>(d, U, U32, mu, parity, (float)beta, k0, k1, sweep);
         else
-            k_wilson32<0><<<nb, kWilsonThreads, 0, s>>>(d, U, mu, parity, (float)beta, k0, k1, sweep);
+            k_wilson32<0><<<nb, kWilsonThreads, 0, s>>>(d, U, U32, mu, parity, (float)beta, k0, k1, sweep);
     } else if (overrelax) {
         k_wilson<1><<<nb, kWilsonThreads, 0, s>>>(d, U, mu, parity, beta, k0, k1, sweep);
     } else {
