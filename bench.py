@@ -277,7 +277,11 @@ def run_ours(args, dims):
     iters = sum(r["iters"] for r in info)
     T, iters = reduce_over_ranks(pg, T, iters)
     value = iters / T
-    launches = sum(3 + 5 * max(r["iters"], 1) for r in info)
+    # kernels of the timed region, per step: lgf_set_links (pack and check, G = 1),
+    # then the graph of lgf_fix (packed parts and Delta of the input, then per loop
+    # pass the z,t kernel, the inverse x,y + g kernel, the update, Delta and the
+    # loop control)
+    launches = sum(2 + 2 + 5 * max(r["iters"], 1) for r in info)
     ttt = {}
     for k, r in enumerate(info):
         ttt.setdefault(str(EPS[k % len(EPS)]), dict(iters=r["iters"], ms=1000 * per_step[k], F=r["F"],
@@ -308,7 +312,7 @@ def run_ours(args, dims):
         Tm = sum(mper)
         mit = sum(r["iters"] for r in minfo)
         Tm, mit = reduce_over_ranks(pg, Tm, mit)
-        launches += sum(5 + 5 * max(r["iters_fp32"], 1) + 5 * max(r["iters_fp64"], 1) for r in minfo)
+        mixed_launches = sum(2 + 5 + 5 * max(r["iters_fp32"], 1) + 5 * max(r["iters_fp64"], 1) for r in minfo)
         mttt = {}
         for k, r in enumerate(minfo):
             e = str(EPS[k % len(EPS)])
@@ -317,6 +321,7 @@ def run_ours(args, dims):
                                     F=r["F"], theta=r["theta"], converged=r["converged"],
                                     F_rel_diff_vs_fp64=(abs(r["F"] / f64 - 1) if f64 else None)))
         mixed = {"value": mit / Tm, "unit": "iters/s", "ms_per_step": 1000 * Tm / args.steps,
+                 "gpu_launches": mixed_launches,
                  "speedup_time_to_theta_vs_fp64": T / Tm, "time_to_theta": mttt}
         # the FP32 phase run down to theta < 1e-13, where FP32 iterations stop tracking FP64 ones
         latm.set_switch_tol(1e-13)
