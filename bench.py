@@ -312,7 +312,9 @@ def run_ours(args, dims):
         Tm = sum(mper)
         mit = sum(r["iters"] for r in minfo)
         Tm, mit = reduce_over_ranks(pg, Tm, mit)
-        mixed_launches = sum(2 + 5 + 5 * max(r["iters_fp32"], 1) + 5 * max(r["iters_fp64"], 1) for r in minfo)
+        # set_links; FP32 start (copy, parts, Delta); FP32 passes of 7 kernels (with the two
+        # refresh kernels); the switch (3) and the FP64 start (2); FP64 passes of 5
+        mixed_launches = sum(2 + 3 + 7 * max(r["iters_fp32"], 1) + 5 + 5 * max(r["iters_fp64"], 1) for r in minfo)
         mttt = {}
         for k, r in enumerate(minfo):
             e = str(EPS[k % len(EPS)])
