@@ -345,8 +345,8 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson(Lat d, double2* __res
 
 // ---------------------------------------------------------------- FP32 staples
 
-// The same update with the staples, W and the SU(2) draws in FP32 (links stay
-// FP64 in memory: R is applied to the FP64 link and the link re-orthonormalised
+// The same update with the staples, W, the SU(2) draws and the rotation of the
+// link in FP32 (links stay FP64 in memory: the rotated link is re-orthonormalised
 // in FP64, so it stays in SU(3) to FP64 rounding).  A Markov chain of its own:
 // the heat bath samples exp((beta/3) Re Tr(U A)) with A known to FP32 rounding,
 // and its uniforms take the top 24 bits of the same Philox words.
@@ -398,10 +398,10 @@ __device__ __noinline__ void su2_draw_f(float b, uint32_t k0, uint32_t k1, uint3
     y[1] = y[2] = y[3] = 0.0f;
 }
 
-// rows i, j of the FP32 matrix w and of the FP64 link u <- R (rows i, j)
+// rows i, j of w and of the link u (both FP32 here) <- R (rows i, j)
 template <int MODE, int I, int J>
-__device__ __forceinline__ void subgroup32(C* u, cx<float>* w, float beta23, uint32_t k0, uint32_t k1, uint32_t link,
-                                           uint32_t sweep, int sub)
+__device__ __forceinline__ void subgroup32(cx<float>* u, cx<float>* w, float beta23, uint32_t k0, uint32_t k1,
+                                           uint32_t link, uint32_t sweep, int sub)
 {
     using F = cx<float>;
     const F wii = w[3 * I + I], wjj = w[3 * J + J], wij = w[3 * I + J], wji = w[3 * J + I];
@@ -429,8 +429,7 @@ __device__ __forceinline__ void subgroup32(C* u, cx<float>* w, float beta23, uin
         R11 = cmac(cmul(D10, D01), D11, D11);
     }
     rot_rows<I, J>(w, R00, R01, R10, R11);
-    rot_rows<I, J>(u, mk((double)R00.re, (double)R00.im), mk((double)R01.re, (double)R01.im),
-                   mk((double)R10.re, (double)R10.im), mk((double)R11.re, (double)R11.im));
+    rot_rows<I, J>(u, R00, R01, R10, R11);
 }
 
 // U32: an FP32 copy of rows 0,1 of every link ([mu][6][V]), read for the staples
@@ -466,9 +465,12 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __r
     mm<float>(uf, A, w);
     const uint32_t link = (uint32_t)mu * (uint32_t)V + (uint32_t)s;
     const float beta23 = beta * (2.0f / 3.0f);
-    subgroup32<MODE, 0, 1>(u, w, beta23, k0, k1, link, sweep, 0);
-    subgroup32<MODE, 0, 2>(u, w, beta23, k0, k1, link, sweep, 1);
-    subgroup32<MODE, 1, 2>(u, w, beta23, k0, k1, link, sweep, 2);
+    subgroup32<MODE, 0, 1>(uf, w, beta23, k0, k1, link, sweep, 0);
+    subgroup32<MODE, 0, 2>(uf, w, beta23, k0, k1, link, sweep, 1);
+    subgroup32<MODE, 1, 2>(uf, w, beta23, k0, k1, link, sweep, 2);
+    // back to FP64 and onto SU(3) there: the stored link is unitary to FP64 rounding
+#pragma unroll
+    for (int e = 0; e < 6; e++) u[e] = mk((double)uf[e].re, (double)uf[e].im);
     reunit(u);
 #pragma unroll
     for (int e = 0; e < 6; e++) {
