@@ -320,13 +320,14 @@ int lgf_plaquette(lgf_ctx* ctx, double* P);
 /*
  * lgf_set_generator_precision: 64 (default) or 32.  With 32 the staples, W, the
  * SU(2) draws and the rotation of each link in lgf_wilson_sweeps are FP32
- * (staples from an FP32 copy of the links that the sweeps keep current, uniforms
- * from the top 24 bits of the same Philox words); the links stay FP64 in memory,
- * each re-orthonormalised in FP64 after its update.  A chain of its own, with the
- * Wilson action's equilibrium up to FP32 rounding, about 12x faster on GB300,
- * where FP64 arithmetic runs at 1/64 of the FP32 rate (32^4: 1.55 against 19.6 ms
- * per heat-bath sweep; the copy takes 4 V x 48 bytes of device memory); the FP64
- * generator is the one that matches the reference to rounding.
+ * (the links and their staples read from an FP32 copy of the links that the
+ * sweeps keep current, uniforms from the top 24 bits of the same Philox words);
+ * the links stay FP64 in memory, rows 0,1 of each re-orthonormalised in FP64
+ * after its update.  A chain of its own, with the Wilson action's equilibrium up
+ * to FP32 rounding, about 15x faster on GB300, where FP64 arithmetic runs at 1/64
+ * of the FP32 rate (32^4: 1.30 against 19.6 ms per heat-bath sweep; the copy
+ * takes 4 V x 48 bytes of device memory); the FP64 generator is the one that
+ * matches the reference to rounding.
  */
 int lgf_set_generator_precision(lgf_ctx* ctx, int bits);
 

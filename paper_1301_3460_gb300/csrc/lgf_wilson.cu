@@ -281,8 +281,8 @@ __device__ __forceinline__ void subgroup(C* u, C* w, double beta23, uint32_t k0,
     rot_rows<I, J>(w, R00, R01, R10, R11);
 }
 
-// Gram-Schmidt of rows 0, 1 and row 2 = conj(row0 x row1)
-__device__ __forceinline__ void reunit(C* m)
+// Gram-Schmidt of rows 0, 1 (row 2 untouched)
+__device__ __forceinline__ void orthonormal_rows01(C* m)
 {
     double n0 = 0;
 #pragma unroll
@@ -302,6 +302,12 @@ __device__ __forceinline__ void reunit(C* m)
     n1 = rsqrt(n1);
 #pragma unroll
     for (int c = 0; c < 3; c++) m[3 + c] = m[3 + c] * n1;
+}
+
+// Gram-Schmidt of rows 0, 1 and row 2 = conj(row0 x row1)
+__device__ __forceinline__ void reunit(C* m)
+{
+    orthonormal_rows01(m);
     complete_row2(m, m + 6);
 }
 
@@ -343,11 +349,12 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson(Lat d, double2* __res
     }
 }
 
-// ---------------------------------------------------------------- FP32 staples
+// ---------------------------------------------------------------- FP32 generator
 
 // The same update with the staples, W, the SU(2) draws and the rotation of the
-// link in FP32 (links stay FP64 in memory: the rotated link is re-orthonormalised
-// in FP64, so it stays in SU(3) to FP64 rounding).  A Markov chain of its own:
+// link in FP32, all read from the FP32 copy (links stay FP64 in memory: rows 0,1
+// of the rotated link are re-orthonormalised in FP64, so the stored link stays in
+// SU(3) to FP64 rounding).  A Markov chain of its own:
 // the heat bath samples exp((beta/3) Re Tr(U A)) with A known to FP32 rounding,
 // and its uniforms take the top 24 bits of the same Philox words.
 
@@ -458,10 +465,8 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __r
         d32.ne = 6;
         staple_sum<float>(d32, U32, mu, s, c, A);
     }
-    C u[9];
-    load3<double>(U, V, ne, mu, s, u);
-#pragma unroll
-    for (int e = 0; e < 9; e++) uf[e] = mk((float)u[e].re, (float)u[e].im);
+    // the link itself from the FP32 copy, row 2 rebuilt in FP32
+    load3<float>(U32, V, 6, mu, s, uf);
     mm<float>(uf, A, w);
     const uint32_t link = (uint32_t)mu * (uint32_t)V + (uint32_t)s;
     const float beta23 = beta * (2.0f / 3.0f);
@@ -469,15 +474,17 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson32(Lat d, double2* __r
     subgroup32<MODE, 0, 2>(uf, w, beta23, k0, k1, link, sweep, 1);
     subgroup32<MODE, 1, 2>(uf, w, beta23, k0, k1, link, sweep, 2);
     // back to FP64 and onto SU(3) there: the stored link is unitary to FP64 rounding
+    C u[9];
 #pragma unroll
     for (int e = 0; e < 6; e++) u[e] = mk((double)uf[e].re, (double)uf[e].im);
-    reunit(u);
+    orthonormal_rows01(u);
 #pragma unroll
     for (int e = 0; e < 6; e++) {
         st<double>(U + (size_t)(mu * ne + e) * V + s, u[e]);
         U32[(size_t)(mu * 6 + e) * V + s] = make_float2((float)u[e].re, (float)u[e].im);
     }
     if (ne == 9) {
+        complete_row2(u, u + 6);
 #pragma unroll
         for (int e = 6; e < 9; e++) st<double>(U + (size_t)(mu * 9 + e) * V + s, u[e]);
     }

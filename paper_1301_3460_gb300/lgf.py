@@ -452,7 +452,8 @@ def _plaquette(self) -> float:
 
 
 def _set_generator_precision(self, bits: int):
-    """64 (default) or 32: arithmetic of the Wilson generator's staples and draws."""
+    """64 (default) or 32: arithmetic of the Wilson generator's staples, draws and
+    rotations (with 32 the links stay FP64 in memory, re-orthonormalised in FP64)."""
     _check(self._lib.lgf_set_generator_precision(self._h, int(bits)), "lgf_set_generator_precision")
 
 
