@@ -409,3 +409,49 @@ def test_delta_is_the_gradient_of_F():
         want = -np.real(np.trace(X @ D[x0])) / (24 * V)
         assert abs(fd - want) < 1e-9 * max(1.0, abs(want)) + 1e-12
         assert abs(want) > 1e-6
+
+
+def test_fixed_point_is_a_local_maximum():
+    """Landau gauge is a maximum of the functional F_U[g] (the display equation of
+    the introduction): after a run to theta < 1e-15, gauge rotations
+    g(x) = exp(t X(x)) with random traceless anti-Hermitian X at every site,
+    applied here with numpy to the oracle's output links, leave F unchanged at
+    first order (the gradient is of order sqrt(theta)) and lower it at second
+    order along every direction tried.  On the unfixed input the first-order
+    change is large, so the check has teeth; a run converging to a saddle or a
+    minimum would fail the second-order check."""
+    from scipy.linalg import expm
+
+    L = (4, 4, 4, 6)
+    V = int(np.prod(L))
+    grid = _grid(L)
+    U0 = inputs.rough_gauge_field(L, 0.3, 91)
+    r = orc.fix(L, U0, alpha=0.08, tol=1e-15, max_iter=3000)
+    assert r["converged"]
+
+    def F_of(U):
+        return np.real(np.trace(U, axis1=-2, axis2=-1)).sum() / (12 * V)
+
+    def rotated(U, g):
+        gg = g.reshape(grid + (3, 3))
+        out = np.empty_like(U)
+        for mu in range(4):
+            gn = np.roll(gg, -1, axis=3 - mu).reshape(V, 3, 3)  # g(x + mu)
+            out[mu] = g @ U[mu] @ dag(gn)
+        return out
+
+    rng = np.random.default_rng(17)
+    h = 1e-3
+    for U, fixed in ((r["U"], True), (U0, False)):
+        U = np.asarray(U).reshape(4, V, 3, 3)
+        F0 = F_of(U)
+        for _ in range(3):
+            X = 1j * inputs.random_su3_algebra(rng, (V,))
+            Fp, Fm = F_of(rotated(U, expm(h * X))), F_of(rotated(U, expm(-h * X)))
+            first = (Fp - Fm) / (2 * h)
+            second = (Fp + Fm - 2 * F0) / h**2
+            if fixed:
+                assert abs(first) < 2e-8
+                assert second < -0.05
+            else:
+                assert abs(first) > 5e-5
