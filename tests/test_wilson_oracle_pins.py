@@ -134,3 +134,63 @@ def test_single_link_update_matches_sweep():
             continue
         assert np.abs(oracle.wilson_link(L, U, s, 0, 5.7, 4, 3) - U1[0, s]).max() < 1e-15
     assert np.array_equal(U, before)
+
+
+def test_single_link_heat_bath_samples_the_local_boltzmann_weight():
+    """With every other link held fixed, repeated heat-bath updates of one link
+    form a Markov chain whose stationary law is exp((beta/3) Re Tr(U A)) dU (Haar
+    measure dU, A the sum of the six staples).  The chain's averages of Re Tr(UA),
+    Im Tr(UA) and (Re Tr(UA))^2 must equal those of Haar-random SU(3) matrices
+    reweighted by that factor.  A rotation applied on the wrong side, a staple of
+    the wrong orientation or a wrong subgroup projection samples another law.
+    The staple sum is written out here from the plaquettes that contain the
+    link, and checked by overrelaxation, which keeps Re Tr(UA) exactly."""
+    L = (4, 4, 4, 4)
+    V = int(np.prod(L))
+    grid = tuple(L[::-1])
+    U = inputs.rough_gauge_field(L, 0.7, seed=8).reshape(4, V, 3, 3).copy()
+    site, mu, beta = 37, 2, 2.0
+
+    def dag(m):
+        return np.conj(np.swapaxes(m, -1, -2))
+
+    def shift(s, nu, k):
+        t, z, y, x = np.unravel_index(s, grid)
+        c = [x, y, z, t]
+        c[nu] = (c[nu] + k) % L[nu]
+        return int(np.ravel_multi_index((c[3], c[2], c[1], c[0]), grid))
+
+    # Re Tr of the plaquettes through U_mu(x) = Re Tr(U_mu(x) A)
+    A = np.zeros((3, 3), complex)
+    xp = shift(site, mu, 1)
+    for nu in range(4):
+        if nu == mu:
+            continue
+        A += U[nu, xp] @ dag(U[mu, shift(site, nu, 1)]) @ dag(U[nu, site])
+        xm = shift(site, nu, -1)
+        A += dag(U[nu, shift(xp, nu, -1)]) @ dag(U[mu, xm]) @ U[nu, xm]
+    u_or = oracle.wilson_link(L, U, site, mu, beta, 5, 0, mode=1)
+    assert abs(np.trace(u_or @ A).real - np.trace(U[mu, site] @ A).real) < 1e-12
+    assert np.abs(u_or - U[mu, site]).max() > 0.1
+
+    n = 20000
+    tr = np.empty(n, complex)
+    for k in range(n):
+        U[mu, site] = oracle.wilson_link(L, U, site, mu, beta, 11, k)
+        tr[k] = np.trace(U[mu, site] @ A)
+    H = inputs.haar_su3(np.random.default_rng(3), 400000)
+    th = np.einsum("nij,ji->n", H, A)
+    lw = beta / 3 * th.real
+    w = np.exp(lw - lw.max())
+    errs = []
+    for chain, haar in ((tr.real, th.real), (tr.imag, th.imag), (tr.real ** 2, th.real ** 2)):
+        want = (w * haar).sum() / w.sum()
+        err_w = np.sqrt((w * w * (haar - want) ** 2).sum()) / w.sum()
+        batches = chain.reshape(100, -1).mean(1)  # batch means absorb the chain's autocorrelation
+        err_c = batches.std() / np.sqrt(len(batches))
+        errs.append(np.hypot(err_w, err_c))
+        assert abs(chain.mean() - want) < 5 * errs[-1]
+    # the check has teeth at this resolution: beta off by 10% moves <Re Tr(UA)> by
+    # many standard errors
+    w2 = np.exp(0.9 * lw - (0.9 * lw).max())
+    assert abs((w2 * th.real).sum() / w2.sum() - tr.real.mean()) > 10 * errs[0]
