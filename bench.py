@@ -458,7 +458,7 @@ def run_ours(args, dims):
             msw = e0.elapsed_time(e1) / args.steps
             gf = roofline.WILSON_FLOPS_PER_LINK * 4 * V / msw / 1e6
             wilson[lab] = {"ms_per_sweep": msw, "gflops": gf, "frac_fp64_peak": gf / FP64_PEAK_GFLOPS}
-        # the FP32-staple generator
+        # the FP32 generator (its own chain; links re-orthonormalised in FP64)
         lw.set_generator_precision(32)
         for lab, nhb, nor in (("heatbath_fp32", 1, 0), ("overrelax_fp32", 0, 1)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
