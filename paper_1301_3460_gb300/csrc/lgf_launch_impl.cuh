@@ -1,8 +1,11 @@
 // Definitions of the templated launchers of lgf_launch.h; included by the
 // per-precision translation units, which instantiate them.
 #pragma once
+#include <type_traits>
+
 #include "lgf_aux.cuh"
 #include "lgf_launch.h"
+#include "lgf_zt_lines.cuh"
 
 namespace lgf {
 
@@ -47,6 +50,15 @@ template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh)
     if ((e = allow_max_smem(k_xyinv_g<T, T>, optin))) return e;
     if ((e = allow_max_smem(k_xy_fft<T, false>, optin))) return e;
     if ((e = allow_max_smem(k_xy_fft<T, true>, optin))) return e;
+    if constexpr (std::is_same<T, float>::value) {
+        const void* lines[] = {(const void*)k_zt_lines<8, 4>,  (const void*)k_zt_lines<8, 8>,
+                               (const void*)k_zt_lines<8, 16>, (const void*)k_zt_lines<16, 4>,
+                               (const void*)k_zt_lines<16, 8>, (const void*)k_zt_lines<16, 16>,
+                               (const void*)k_zt_lines<32, 4>, (const void*)k_zt_lines<32, 8>,
+                               (const void*)k_zt_lines<32, 16>};
+        for (const void* k : lines)
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin))) return e;
+    }
     return allow_max_smem(k_zt<T>, optin);
 }
 
@@ -72,6 +84,14 @@ template <typename T>
 void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl)
 {
     dim3 grid(d.L[0] / sh.zt.xw, d.L[1], 4);
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 phase, Lz = Lt <= 32: whole lines in registers
+        const int n = zt_lines_n(d, sh.zt.xw);
+        if (n != 0 && tb.mult32 != nullptr) {
+            launch_zt_lines(n, sh.zt.xw, s, d, Fd, ctl, tb.mult32);
+            return;
+        }
+    }
     k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.zt, Fd, ctl, tw_of<T>(tb, 2), tw_of<T>(tb, 3),
                                                       mult_of<T>(tb), tb.s2[0], tb.s2[1], tb.s2[2], tb.s2[3],
                                                       tb.p2max);

@@ -58,6 +58,36 @@ def test_mixed_full_size_against_fp64_gpu():
     assert err < 1e-4
 
 
+@pytest.mark.parametrize("autotune", [False, True])
+@pytest.mark.parametrize("L,seed", [((8, 8, 8, 8), 1001), ((16, 16, 16, 16), 1601), ((8, 8, 32, 32), 3301)])
+def test_fp32_phase_follows_the_fp64_iteration(L, seed, autotune):
+    """The FP32 phase is the FP64 iteration to FP32 rounding: theta_n of its first
+    eight updates matches the oracle's to 1e-5 relative (measured 5e-8 to 1.3e-7:
+    a few FP32 roundings) and the links after them (re-projected in FP64) to 1e-4
+    (measured 1.2e-6 to 2.3e-6), with the default launch shapes and with the
+    autotuned ones (these extents, Lz = Lt <= 32, take the register-line z,t
+    transform).  A wrong mode anywhere in the FP32 Delta, transforms,
+    accelerator or update shows at O(1)."""
+    U = inputs.rough_gauge_field(L, 0.3, seed)
+    ref = orc.fix(L, U, alpha=0.08, tol=0.0, max_iter=8, history=True)
+    with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_switch_tol(0.0)
+        lat.set_links(U)
+        if autotune:
+            lat.autotune()
+            lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=8)
+        hist = lat.history()
+        Um = lat.get_links()
+    assert r["iters"] == 8 and r["iters_fp64"] == 0
+    th64, th32 = ref["history"][:8, 0], hist[:8, 0]
+    rel = np.abs(th32 / th64 - 1)
+    print("%s autotune=%s: theta_0..7 max rel diff %.2e, links %.2e" % (L, autotune, rel.max(),
+                                                                        np.abs(Um - ref["U"]).max()))
+    assert rel.max() < 1e-5
+    assert np.max(np.abs(Um - ref["U"])) < 1e-4
+
+
 def test_mixed_max_iter_in_fp32_phase_keeps_progress():
     L = (8, 8, 8, 8)
     U = inputs.rough_gauge_field(L, 0.3, 5)
