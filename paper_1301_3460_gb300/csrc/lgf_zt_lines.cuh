@@ -3,7 +3,7 @@
 // z and t of the four packed Delta fields, the accelerator p2max/(p2(k) V) with the
 // zero mode removed, inverse FFT along t and z), organised for an FP32 phase whose
 // fields sit in L2: one thread transforms one line of N points held in registers
-// (radix 2, twiddles as immediates), so a launch has four barriers instead of one
+// (radix 2, twiddles as compile-time constants), so a launch has four barriers instead of one
 // per Stockham stage and no twiddle loads.
 //
 // One block per (x-chunk of XW columns, y, field), XW * N threads.  The tile holds
