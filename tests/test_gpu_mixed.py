@@ -65,8 +65,8 @@ def test_fp32_phase_follows_the_fp64_iteration(L, seed, autotune):
     eight updates matches the oracle's to 1e-5 relative (measured 5e-8 to 1.3e-7:
     a few FP32 roundings) and the links after them (re-projected in FP64) to 1e-4
     (measured 1.2e-6 to 2.3e-6), with the default launch shapes and with the
-    autotuned ones (these extents, Lz = Lt <= 32, take the register-line z,t
-    transform).  A wrong mode anywhere in the FP32 Delta, transforms,
+    autotuned ones (at the default pencil width of 8 columns these extents,
+    Lz = Lt <= 32, take the register-line z,t transform).  A wrong mode anywhere in the FP32 Delta, transforms,
     accelerator or update shows at O(1)."""
     U = inputs.rough_gauge_field(L, 0.3, seed)
     ref = orc.fix(L, U, alpha=0.08, tol=0.0, max_iter=8, history=True)
