@@ -27,8 +27,8 @@
  *                  p2(k) = sum_mu 4 sin^2(pi k_mu / L_mu),  p2max = max_k p2(k)
  *       g(x)     = reunit(1 + (alpha/2) Delta~(x))           (row Gram-Schmidt)
  *       U_mu(x) <- g(x) U_mu(x) g^dag(x+mu),  G(x) <- g(x) G(x)
- *     Rows 0,1 carry the link (the "12 real number representation" of the
- *     paper's GPU code); row 2 is recomputed as conj(row0 x row1) after every
+ *     Rows 0,1 carry the link (the 12-real link storage of the paper's GPU
+ *     code); row 2 is recomputed as conj(row0 x row1) after every
  *     update, for links and for the accumulated gauge transformation G.
  *
  * Storage: a link field is [4][V][3][3] complex double (mu-major, then site,
