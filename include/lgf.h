@@ -80,7 +80,9 @@ typedef enum {
  * shared-memory FFT tiles (the four fields of one xy-plane plus one of scratch,
  * and two buffers of one z,t pencil) must fit in 220 KiB: for FP64 and mixed
  * contexts Lx*Ly <= 2816 and Lt*(Lz + 1) <= 7040 (e.g. 96x24 planes, 64x96 or
- * 128x48 pencils); else LGF_ERR_UNSUPPORTED_DIMS.  flags: LGF_FP64 or
+ * 128x48 pencils); and 24 V must fit a signed 32-bit offset (V <= 89,478,485
+ * sites, e.g. 96^4); else LGF_ERR_UNSUPPORTED_DIMS.  Extents are checked before
+ * any CUDA call.  flags: LGF_FP64 or
  * LGF_MIXED, optionally | LGF_NO_GAUGE, | LGF_PLAIN_SD, | LGF_LINKS18 or | LGF_LINKS8.  *out receives the
  * context.
  */

@@ -1,0 +1,68 @@
+"""lgf_create's checks of its arguments, on the CPU: the extents and the tile
+limits that include/lgf.h documents are the ones the library applies, and
+argument errors are status codes.  Without a GPU an accepted lattice fails
+later, with LGF_ERR_CUDA; the test is skipped where a GPU would let it allocate."""
+import ctypes
+import itertools
+
+import pytest
+
+from paper_1301_3460_gb300 import lgf
+
+LENGTHS = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128)
+
+
+def create(dims, flags=lgf.LGF_FP64):
+    lib = lgf.load()
+    d = (ctypes.c_int * 4)(*dims)
+    h = ctypes.c_void_p()
+    st = lib.lgf_create(d, flags, ctypes.byref(h))
+    if st == lgf.LGF_OK:
+        lib.lgf_destroy(h)
+    return st
+
+
+@pytest.fixture(scope="module", autouse=True)
+def no_gpu():
+    if create((4, 4, 4, 4)) != lgf.LGF_ERR_CUDA:
+        pytest.skip("a usable GPU is present: accepted lattices would be allocated")
+
+
+def documented_ok(L):
+    """The header's rule: every extent in LENGTHS, Lx*Ly <= 2816,
+    Lt*(Lz + 1) <= 7040, and 24 V within a signed 32-bit offset."""
+    Lx, Ly, Lz, Lt = L
+    V = Lx * Ly * Lz * Lt
+    return Lx * Ly <= 2816 and Lt * (Lz + 1) <= 7040 and 24 * V <= 2**31 - 1
+
+
+def test_every_supported_extent_combination():
+    bad = []
+    for L in itertools.product(LENGTHS, repeat=4):
+        want = lgf.LGF_ERR_CUDA if documented_ok(L) else lgf.LGF_ERR_UNSUPPORTED_DIMS
+        for flags in (lgf.LGF_FP64, lgf.LGF_MIXED):
+            st = create(L, flags)
+            if st != want:
+                bad.append((L, flags, st))
+    assert not bad, bad[:10]
+
+
+@pytest.mark.parametrize("L", [(10, 8, 8, 8), (8, 8, 8, 0), (8, -4, 8, 8), (256, 4, 4, 4), (8, 8, 2, 8),
+                               (8, 8, 8, 20)])
+def test_unsupported_lengths(L):
+    assert create(L) == lgf.LGF_ERR_UNSUPPORTED_DIMS
+
+
+def test_argument_errors():
+    lib = lgf.load()
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(8, 8, 8, 8)
+    assert lib.lgf_create(None, 0, ctypes.byref(h)) == lgf.LGF_ERR_ARG
+    assert lib.lgf_create(d, 0, None) == lgf.LGF_ERR_ARG
+    assert create((8, 8, 8, 8), 1 << 10) == lgf.LGF_ERR_ARG
+    assert create((8, 8, 8, 8), lgf.LGF_LINKS18 | lgf.LGF_LINKS8) == lgf.LGF_ERR_ARG
+    # calls on a null context are argument errors, not crashes
+    assert lib.lgf_fix(None, 0.08, 1e-15, 10, None, None, None) == lgf.LGF_ERR_ARG
+    assert lib.lgf_set_links(None, None, 0) == lgf.LGF_ERR_ARG
+    assert lib.lgf_get_links(None, None, 0) == lgf.LGF_ERR_ARG
+    lib.lgf_destroy(None)
