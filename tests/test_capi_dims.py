@@ -66,3 +66,38 @@ def test_argument_errors():
     assert lib.lgf_set_links(None, None, 0) == lgf.LGF_ERR_ARG
     assert lib.lgf_get_links(None, None, 0) == lgf.LGF_ERR_ARG
     lib.lgf_destroy(None)
+
+
+def test_noalloc_limits():
+    """lgf_accelerate_noalloc takes the extents of lgf_create up to V = 65536
+    sites; larger lattices are refused before any CUDA call."""
+    lib = lgf.load()
+    buf = (ctypes.c_double * 2)()
+    bad = []
+    for L in itertools.product(LENGTHS, repeat=4):
+        V = L[0] * L[1] * L[2] * L[3]
+        if V > 4 * 65536:
+            continue
+        want = lgf.LGF_ERR_CUDA if (documented_ok(L) and V <= 65536) else lgf.LGF_ERR_UNSUPPORTED_DIMS
+        st = lib.lgf_accelerate_noalloc((ctypes.c_int * 4)(*L), buf, buf, None)
+        if st != want:
+            bad.append((L, st))
+    assert not bad, bad[:10]
+    assert lib.lgf_accelerate_noalloc(None, buf, buf, None) == lgf.LGF_ERR_ARG
+
+
+def test_batch_create_checks_every_member():
+    lib = lgf.load()
+    h = ctypes.c_void_p()
+
+    def batch(dims_list, flags=lgf.LGF_MIXED):
+        flat = (ctypes.c_int * (4 * len(dims_list)))(*[v for d in dims_list for v in d])
+        return lib.lgf_batch_create(len(dims_list), flat, flags, ctypes.byref(h))
+
+    # members are created in order and the first failure is returned: without a
+    # GPU an accepted member fails with LGF_ERR_CUDA, so refused extents go first
+    assert batch([(8, 8, 8, 8), (16, 16, 16, 16)]) == lgf.LGF_ERR_CUDA
+    assert batch([(10, 16, 16, 16), (8, 8, 8, 8)]) == lgf.LGF_ERR_UNSUPPORTED_DIMS
+    assert batch([(128, 128, 8, 8), (8, 8, 8, 8)]) == lgf.LGF_ERR_UNSUPPORTED_DIMS
+    assert batch([(8, 8, 8, 8)], flags=1 << 10) == lgf.LGF_ERR_ARG
+    assert lib.lgf_batch_create(0, (ctypes.c_int * 4)(8, 8, 8, 8), 0, ctypes.byref(h)) == lgf.LGF_ERR_ARG
