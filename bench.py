@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-links18", action="store_true")
     ap.add_argument("--no-links8", action="store_true")
     ap.add_argument("--no-wilson", action="store_true")
+    ap.add_argument("--no-cpu-fix", action="store_true", help="skip the oracle's full-size fix in cpu_baseline")
+    ap.add_argument("--no-48", action="store_true", help="skip the 48^4 FP64-vs-mixed leg")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 58-lattice ensemble leg")
     ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble; "
                          "wilson: Wilson-action configuration generation (heat bath + overrelaxation)")
@@ -66,6 +69,14 @@ def parse():
     ap.add_argument("--switch-tol", type=float, default=1e-6,
                     help="theta that ends the FP32 phase of --workload ensemble (1e-6 as specified; 1e-13 deep)")
     return ap.parse_args()
+
+
+def bench_config(dims, args, ws):
+    """The workload description printed by both arms (same keys, same values)."""
+    V = int(np.prod(dims))
+    return {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol, "eps": list(EPS),
+            "l2": "inputs larger than L2 (%.0f MB of links per configuration)" % (4 * V * 12 * 8 / 1e6),
+            "parallelism": "replicas" if ws > 1 else "single"}
 
 
 def workload(dims):
@@ -216,7 +227,7 @@ def run_reference(args, dims):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol},
+        "config": bench_config(dims, args, 1),
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
                          "sample": "one oracle iteration per step on the %s configurations (eps %s)" % (
                              "x".join(map(str, dims)), "/".join(map(str, EPS)))},
@@ -532,6 +543,22 @@ def run_ours(args, dims):
         Te, n_e2e = reduce_over_ranks(pg, Te, n_e2e)
         e2e = {"value": n_e2e / Te, "unit": "iters/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    # 48^4 (radix-3 FFT lengths): FP64 against mixed precision on one configuration
+    big48 = None
+    if not args.no_48 and not args.no_mixed:
+        try:
+            big48 = run_48(args, stream, rank)
+        except Exception as e:  # the main line stands without this leg
+            big48 = {"error": repr(e)}
+
+    # the batched ensemble of uneven lattices in one graph launch, switch 1e-6 and 1e-13
+    ens = None
+    if not args.no_ensemble and not args.no_mixed:
+        try:
+            ens = ensemble_leg(args, stream, rank)
+        except Exception as e:
+            ens = {"error": repr(e)}
+
     # per-kernel durations (CUDA events around each launch) on the eps = 0.3 configuration
     lat.set_links(dev[1])
     ms = lat.time_kernels(args.alpha, n_iter=8, precision=64)
@@ -584,9 +611,13 @@ def run_ours(args, dims):
             t0 = time.perf_counter()
             rs = orc.fix(Ls, Us, alpha=args.alpha, tol=args.tol, max_iter=args.max_iter)
             cpu["time_to_theta_%s_s" % "x".join(map(str, Ls))] = {"s": time.perf_counter() - t0, "iters": rs["iters"]}
-        it03 = ttt.get(str(EPS[1]), {}).get("iters")
-        if it03:
-            cpu["time_to_theta_%s_derived_s" % "x".join(map(str, dims))] = it03 * dt / r["iters"]
+        # the full-size fix to theta < tol, measured (about 15 s on 16 host cores at 32^4)
+        if not args.no_cpu_fix:
+            t0 = time.perf_counter()
+            rs = orc.fix(dims, host[1], alpha=args.alpha, tol=args.tol, max_iter=args.max_iter)
+            cpu["time_to_theta_%s_s" % "x".join(map(str, dims))] = {
+                "s": time.perf_counter() - t0, "iters": rs["iters"], "converged": rs["converged"],
+                "F_rel_diff_vs_gpu": abs(rs["F"] / ttt[str(EPS[1])]["F"] - 1) if str(EPS[1]) in ttt else None}
 
     lat.close()
     if rank == 0:
@@ -594,12 +625,10 @@ def run_ours(args, dims):
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload(dims), "dims": list(dims), "alpha": args.alpha, "tol": args.tol,
-                       "eps": list(EPS), "l2": "inputs larger than L2 (%.0f MB of links per configuration)"
-                       % (4 * V * 12 * 8 / 1e6), "parallelism": "replicas" if ws > 1 else "single"},
+            "config": bench_config(dims, args, ws),
             "time_to_theta": ttt, "mixed": mixed, "links18": links18, "links8": links8, "diff": diff,
             "plain_sd_16x4": plain,
-            "wilson_generation": wilson,
+            "wilson_generation": wilson, "fix_48x4": big48, "ensemble": ens,
             "roofline": roof, "kernels": kernels, "hbm_iteration": hbm_iter, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
@@ -610,6 +639,99 @@ def run_ours(args, dims):
 
 
 ENSEMBLE = ((32, (16, 16, 16, 16)), (16, (24, 24, 24, 24)), (8, (32, 32, 32, 64)), (2, (48, 48, 48, 96)))
+
+
+def run_48(args, stream, rank):
+    """One 48^4 configuration (eps = 0.3, drawn on the GPU) fixed in FP64 and in
+    mixed precision (switch 1e-6 and 1e-13), each after an untimed warm-up fix:
+    time-to-theta, iterations, F of the mixed runs relative to FP64 and the
+    largest link difference (the residual global rotation, reading of Gribov
+    copies)."""
+    import torch
+
+    from paper_1301_3460_gb300 import inputs, lgf
+
+    L = (48, 48, 48, 48)
+    U = inputs.rough_gauge_field_cuda(L, 0.3, 4801 + 1000 * rank)
+    out = {"dims": list(L), "eps": 0.3}
+
+    def timed(lat):
+        lat.set_links(U)
+        lat.fix(args.alpha, args.tol, args.max_iter)  # warm-up (autotuned shapes, graph)
+        lat.set_links(U)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = lat.fix(args.alpha, args.tol, args.max_iter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    with lgf.Lattice(L, stream=stream) as l64:
+        l64.set_links(U)
+        l64.autotune()
+        r64, ms64 = timed(l64)
+        U64 = l64.get_links(device="cuda")
+    out["fp64"] = {"ms": ms64, "iters": r64["iters"], "F": r64["F"], "converged": r64["converged"],
+                   "iters_per_s": 1000.0 * r64["iters"] / ms64}
+    with lgf.Lattice(L, mixed=True, stream=stream) as lm:
+        lm.set_links(U)
+        lm.autotune()
+        for sw in (1e-6, 1e-13):
+            lm.set_switch_tol(sw)
+            rm, msm = timed(lm)
+            Um = lm.get_links(device="cuda")
+            out["mixed_switch_%g" % sw] = {
+                "ms": msm, "iters_fp32": rm["iters_fp32"], "iters_fp64": rm["iters_fp64"], "F": rm["F"],
+                "converged": rm["converged"], "F_rel_diff_vs_fp64": abs(rm["F"] / r64["F"] - 1),
+                "max_link_diff_vs_fp64": float((Um - U64).abs().max().item()),
+                "speedup_vs_fp64": ms64 / msm}
+            del Um
+    del U64, U
+    torch.cuda.empty_cache()
+    return out
+
+
+def ensemble_leg(args, stream, rank):
+    """The 58-lattice ensemble (32 x 16^4, 16 x 24^4, 8 x 32^3x64, 2 x 48^3x96, eps
+    uniform in [0.15, 0.5] from seed 5000, member i seeded 5000 + i), mixed
+    precision, one graph launch per pass: one warm-up pass (autotuning and graph
+    build), then one timed pass at switch 1e-6 and one at 1e-13."""
+    import torch
+
+    from paper_1301_3460_gb300 import inputs, lgf
+
+    dims = [d for n, d in ENSEMBLE for _ in range(n)]
+    eps = np.random.default_rng(5000).uniform(0.15, 0.5, size=len(dims))
+    dev = [inputs.rough_gauge_field_cuda(d, float(e), 5000 + i + 1000 * rank) for i, (d, e) in enumerate(zip(dims, eps))]
+    out = {"lattices": len(dims), "sites": int(sum(int(np.prod(d)) for d in dims))}
+    with lgf.Batch(dims, mixed=True, stream=stream) as b:
+        def one_pass():
+            for i, u in enumerate(dev):
+                b.set_links(i, u)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = b.fix(args.alpha, args.tol, args.max_iter)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return r, e0.elapsed_time(e1)
+
+        b.set_switch_tol(1e-6)
+        one_pass()  # warm-up
+        for sw in (1e-6, 1e-13):
+            b.set_switch_tol(sw)
+            r, ms = one_pass()
+            tt = np.array(r["t_retire_ms"])
+            out["switch_%g" % sw] = {
+                "ms": ms, "configs_per_hour": len(dims) / ms * 3.6e6,
+                "time_to_theta_ms": {"p50": float(np.percentile(tt, 50)), "p99": float(np.percentile(tt, 99)),
+                                     "max": float(tt.max())},
+                "all_converged": all(st == lgf.LGF_OK for st in r["status"]),
+                "iters_fp32_mean": float(np.mean(r["iters_fp32"])),
+                "iters_fp64_mean": float(np.mean(r["iters_fp64"]))}
+    del dev
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ensemble(args):

@@ -17,6 +17,12 @@
 // fields and tables are overwritten before use.  Two calls whose work overlaps
 // on the GPU (different streams, or different host threads on one device) race
 // on the array.
+//
+// The array's device address is looked up on every call (a lookup allocates
+// nothing): after cudaDeviceReset, or from another context on the same device,
+// the module is loaded again and the array can move, so a cached address could
+// point into memory the caller owns.  The kernel attributes are set on the
+// first call on a device and again whenever the address has changed.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -41,7 +47,7 @@ constexpr size_t kScratchBytes = kCtlOff + (sizeof(Ctl) + 255) / 256 * 256;
 constexpr int kMaxDevices = 64;
 
 std::mutex g_setup_mutex;
-unsigned char* g_scratch[kMaxDevices] = {};  // device address of the array, per device
+unsigned char* g_scratch[kMaxDevices] = {};  // device address at the last set-up, per device
 
 bool length_ok(int L)
 {
@@ -99,16 +105,18 @@ extern "C" int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in,
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LGF_ERR_CUDA;
     unsigned char* base;
     {
-        // Set-up, once per device, with that device current: the host-side name of
-        // the array is not a device address, so take the address from the runtime.
+        // With the device current: the host-side name of the array is not a device
+        // address, so take the address from the runtime, on every call.  Set-up
+        // (kernel attributes) on the first call on this device and whenever the
+        // address differs from the one seen at the last set-up.
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, lgf_noalloc_scratch) != cudaSuccess || !p) return LGF_ERR_CUDA;
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, lgf_noalloc_scratch) != cudaSuccess || !p) return LGF_ERR_CUDA;
+        if (g_scratch[dev] != static_cast<unsigned char*>(p)) {
             if (prepare_kernels<double>(d, sh) != cudaSuccess) return LGF_ERR_CUDA;
             g_scratch[dev] = static_cast<unsigned char*>(p);
         }
-        base = g_scratch[dev];
+        base = static_cast<unsigned char*>(p);
     }
 
     // tables for these extents, written into the array (host copies on the stack)

@@ -272,10 +272,22 @@ def lgf_accelerate_noalloc(dims, Delta_in, Dt_out, stream=None) -> None:
     """Context-free Fourier acceleration into a caller-provided output, with the
     library's static device scratch (no device allocation by the call).
     Delta_in and Dt_out: contiguous torch complex128 CUDA tensors (V, 3, 3)."""
+    import torch
+
     lib = load()
     V = int(np.prod([int(v) for v in dims]))
-    for t in (Delta_in, Dt_out):
-        assert _is_torch(t) and t.is_cuda and t.is_contiguous() and tuple(t.shape) == (V, 3, 3)
+    # the kernels read and write V*9 complex128 values on the current device: refuse
+    # anything else here, before a pointer reaches the library
+    for name, t in (("Delta_in", Delta_in), ("Dt_out", Dt_out)):
+        if not _is_torch(t) or not t.is_cuda:
+            raise TypeError("%s must be a torch CUDA tensor" % name)
+        if t.dtype != torch.complex128:
+            raise TypeError("%s must be complex128, got %s" % (name, t.dtype))
+        if tuple(t.shape) != (V, 3, 3) or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous (%d, 3, 3) tensor, got %s" % (name, V, tuple(t.shape)))
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("%s is on %s, not on the current device cuda:%d"
+                             % (name, t.device, torch.cuda.current_device()))
     raw = getattr(stream, "cuda_stream", stream) or 0
     arr = (ctypes.c_int * 4)(*[int(v) for v in dims])
     _check(lib.lgf_accelerate_noalloc(arr, ctypes.c_void_p(Delta_in.data_ptr()), ctypes.c_void_p(Dt_out.data_ptr()),

@@ -179,6 +179,46 @@ def test_full_size_one_step():
     assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
 
 
+@pytest.fixture(scope="module")
+def bench_lattice():
+    """The benchmark lattice: 32^4, eps = 0.3, seed 3202."""
+    L = (32, 32, 32, 32)
+    return L, inputs.rough_gauge_field(L, 0.3, 3202)
+
+
+def test_full_size_ten_steps(bench_lattice):
+    """32^4 benchmark lattice: links and G after 10 steps against the oracle (1e-13)."""
+    L, U = bench_lattice
+    ref = orc.fix(L, U, alpha=0.08, tol=0.0, max_iter=10)
+    with lgf.Lattice(L) as lat:
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=0.0, max_iter=10)
+        assert r["iters"] == 10
+        assert np.max(np.abs(lat.get_links() - ref["U"])) < 1e-13
+        assert np.max(np.abs(lat.get_gauge() - ref["G"])) < 1e-13
+    assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+
+
+def test_full_size_converges_like_oracle(bench_lattice):
+    """32^4 benchmark lattice run to theta < 1e-15 in both: the iteration count
+    (one apart only when theta_n is within 1e-10 of tol), F to 1e-12 relative,
+    links to 1e-11, and the GPU's G relating its links to the input."""
+    L, U = bench_lattice
+    ref = orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=500, history=True)
+    with lgf.Lattice(L) as lat:
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=500)
+        Ug = lat.get_links()
+        Gg = lat.get_gauge()
+    assert ref["converged"] and r["converged"] and r["theta"] < 1e-15
+    if r["iters"] != ref["iters"]:
+        n = min(r["iters"], ref["iters"])
+        assert abs(r["iters"] - ref["iters"]) == 1 and abs(ref["history"][n, 0] / 1e-15 - 1) < 1e-10
+    assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+    assert np.max(np.abs(Ug - ref["U"])) < 1e-11
+    assert np.max(np.abs(orc.gauge_transform(L, U, Gg) - Ug)) < 1e-12
+
+
 def test_contexts_of_different_sizes_coexist():
     """Creating a context for a small lattice must not break a live one with larger planes."""
     Lb, Ls = (16, 16, 16, 16), (4, 4, 4, 4)
