@@ -62,9 +62,11 @@ def parse():
     ap.add_argument("--no-cpu-fix", action="store_true", help="skip the oracle's full-size fix in cpu_baseline")
     ap.add_argument("--no-48", action="store_true", help="skip the 48^4 FP64-vs-mixed leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 58-lattice ensemble leg")
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson"],
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson", "kernels"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble; "
-                         "wilson: Wilson-action configuration generation (heat bath + overrelaxation)")
+                         "wilson: Wilson-action configuration generation (heat bath + overrelaxation); "
+                         "kernels: the iteration kernels launched one by one (FP64 and FP32), per-kernel times")
+    ap.add_argument("--no-autotune", action="store_true", help="--workload kernels: default launch shapes")
     ap.add_argument("--beta", type=float, default=6.0, help="coupling of --workload wilson")
     ap.add_argument("--switch-tol", type=float, default=1e-6,
                     help="theta that ends the FP32 phase of --workload ensemble (1e-6 as specified; 1e-13 deep)")
@@ -172,7 +174,7 @@ class Clocks:
 
 # ---------------------------------------------------------------- traffic record
 
-KERNEL_SOURCES = ("lgf_common.cuh", "lgf_fft.cuh", "lgf_kernels.cuh")
+KERNEL_SOURCES = ("lgf_common.cuh", "lgf_dft.cuh", "lgf_kernels.cuh")
 
 
 def csrc_hash():
@@ -904,8 +906,40 @@ def run_wilson(args, dims):
     return 0
 
 
+def run_kernels(args, dims):
+    """The iteration kernels of one lattice (eps = 0.3, drawn on the GPU) launched
+    one by one, FP64 and FP32, --steps iterations after --warmup: median event
+    time per launch, algorithmic bytes and flops per second, fraction of the
+    measured HBM peak."""
+    import torch
+
+    from paper_1301_3460_gb300 import inputs, lgf, roofline
+
+    V = int(np.prod(dims))
+    hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    U = inputs.rough_gauge_field_cuda(dims, 0.3, 77)
+    out = {"metric": "iteration kernels, median ms per launch", "dims": list(dims), "autotuned": not args.no_autotune}
+    with lgf.Lattice(dims, mixed=True) as lat:
+        lat.set_links(U)
+        if not args.no_autotune:
+            lat.autotune()
+        for prec in (64, 32):
+            if args.warmup:
+                lat.time_kernels(args.alpha, n_iter=args.warmup, precision=prec)
+            ms = lat.time_kernels(args.alpha, n_iter=max(1, args.steps), precision=prec)
+            per = roofline.per_site(dims, prec)
+            out["fp%d" % prec] = {k: {"ms": ms[k], "gbs": per[k]["bytes"] * V / ms[k] / 1e6,
+                                      "hbm_frac_of_measured": per[k]["bytes"] * V / ms[k] / 1e6 / hbm,
+                                      "gflops": per[k]["flops"] * V / ms[k] / 1e6} for k in ms}
+            out["fp%d_iteration_ms" % prec] = sum(ms.values())
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "kernels":
+        return run_kernels(args, tuple(int(v) for v in args.dims.split(",")))
     if args.workload == "ensemble":
         return run_ensemble(args)
     if args.workload == "wilson":

@@ -77,10 +77,11 @@ typedef enum {
 /*
  * lgf_create: allocate a context for a lattice of extents dims[4].
  * Each extent must be one of 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, and the
- * shared-memory FFT tiles (the four fields of one xy-plane plus one of scratch,
- * and two buffers of one z,t pencil) must fit in 220 KiB: for FP64 and mixed
- * contexts Lx*Ly <= 2816 and Lt*(Lz + 1) <= 7040 (e.g. 96x24 planes, 64x96 or
- * 128x48 pencils); and 24 V must fit a signed 32-bit offset (V <= 89,478,485
+ * shared-memory FFT tiles (the four fields of one xy-plane with rows padded to
+ * Lx + 1, and one z,t pencil one x-column wide with rows padded to Lz + 1 plus
+ * its multipliers) must fit in 220 KiB in FP64: Ly*(Lx + 1) <= 3520 and
+ * Lt*(3 Lz + 2) <= 28160 (e.g. 64x48, 96x32 or 128x24 planes, 96x96, 64x128 or
+ * 128x64 pencils); and 24 V must fit a signed 32-bit offset (V <= 89,478,485
  * sites, e.g. 96^4); else LGF_ERR_UNSUPPORTED_DIMS.  Extents are checked before
  * any CUDA call.  flags: LGF_FP64 or
  * LGF_MIXED, optionally | LGF_NO_GAUGE, | LGF_PLAIN_SD, | LGF_LINKS18 or | LGF_LINKS8.  *out receives the
@@ -281,7 +282,7 @@ int lgf_gluon_pmin_bwd(lgf_ctx* ctx, double gD, double* gU);
  *   Dt_out    device pointer, [V][3][3] complex128, receives the result
  *   cuda_stream  the cudaStream_t to run on (NULL = legacy default stream)
  * The call allocates nothing: its scratch is a file-scope device array of about
- * 4 MiB that every GPU loading the library holds until the process exits.  Each
+ * 5 MiB that every GPU loading the library holds until the process exits.  Each
  * call looks up the array's device address on the current device; the first
  * call on a device (and the first after the array has moved, e.g. after
  * cudaDeviceReset) also sets kernel attributes: make that first call before any

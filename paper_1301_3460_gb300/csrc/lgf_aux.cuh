@@ -173,24 +173,36 @@ static __global__ void k_unpack_full(int V, const double2* __restrict__ g, doubl
     }
 }
 
-// plane-wise FFT along x and y of the four fields (stand-alone stage)
+// plane-wise FFT along x and y of the four fields, in place on Fd (stand-alone
+// stage; one block per xy-plane, the plane tile in shared memory)
 template <typename T, bool INV>
-__global__ void __launch_bounds__(kMaxThreads) k_xy_fft(Lat d, const XyFft F, vec2_t<T>* __restrict__ Fd,
-                                                        const vec2_t<T>* __restrict__ twx,
-                                                        const vec2_t<T>* __restrict__ twy)
+__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xy_fft(Lat d, vec2_t<T>* __restrict__ Fd,
+                                                const vec2_t<T>* __restrict__ twx,
+                                                const vec2_t<T>* __restrict__ twy)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
-    const int P = d.P, V = d.V, s0 = blockIdx.x * P;
-    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
-        const int f = i / P, xy = i - f * P;
-        sm[i] = Fd[(size_t)f * V + s0 + xy];
-    }
-    __syncthreads();
-    fft_xy_fields<T>(F, P, sm, sm + 4 * P, twx, twy, INV ? kInv : kFwd);
-    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
-        const int f = i / P, xy = i - f * P;
-        Fd[(size_t)f * V + s0 + xy] = sm[i];
+    const int P = d.P, V = d.V, Lx = d.L[0], s0 = blockIdx.x * P;
+    const int rsx = plane_rsx(d), fs = plane_fs(d);
+    vec2_t<T>* base = Fd + s0;
+    if (INV) {
+        plane_y_lines<T, true>(d, base, V, Lx, sm, fs, rsx, twy);
+        __syncthreads();
+        tile_x_lines<T, true>(d, sm, twx);
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+            const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
+            base[(size_t)f * V + xy] = sm[f * fs + y * rsx + x];
+        }
+    } else {
+        for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+            const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
+            sm[f * fs + y * rsx + x] = base[(size_t)f * V + xy];
+        }
+        __syncthreads();
+        tile_x_lines<T, false>(d, sm, twx);
+        __syncthreads();
+        plane_y_lines<T, false>(d, sm, fs, rsx, base, V, Lx, twy);
     }
 }
 

@@ -128,37 +128,25 @@ struct lgf_ctx {
 
 namespace {
 
-// Shared-memory FFT tiles: an xy-plane of all four fields plus a scratch of
-// nfc fields, and two buffers of a pencil of xw x-columns over (z, t).
-bool make_shape(const Lat& d, size_t elem, int nt_xy, int nfc, int nt_zt, int xw, Shape* sh)
+// Shared-memory FFT tiles: the four fields of an xy-plane, and one z,t pencil of
+// xw x-columns; thread counts a multiple of 32 up to 256.
+bool make_shape(const Lat& d, size_t elem, int nt_xy, int nt_zt, int xw, Shape* sh)
 {
-    const size_t budget = 220 * 1024;
-    const int P = d.P;
-    if (nfc != 1 && nfc != 2 && nfc != 4) return false;
-    if ((size_t)(4 + nfc) * P * elem > budget) return false;
+    if (nt_xy < 32 || nt_xy > 256 || nt_xy % 32 || nt_zt < 32 || nt_zt > 256 || nt_zt % 32) return false;
+    if (plane_tile_bytes(d, elem) > kTileBudget) return false;
     if (xw < 1 || d.L[0] % xw) return false;
-    const ZtFft Z = make_zt_fft(d.L[2], d.L[3], xw, elem);
-    if (zt_tile_bytes(Z, d.L[3], elem) > budget) return false;
+    if (pencil_tile_bytes(d, xw, elem) > kTileBudget) return false;
     sh->nt_xy = nt_xy;
     sh->nt_zt = nt_zt;
-    XyFft& X = sh->xy;
-    X.px = make_axis_plan(d.L[0]);
-    X.py = make_axis_plan(d.L[1]);
-    X.mx = make_linemap(1u << 30, 0, (unsigned)d.L[0], 1);
-    X.my = make_linemap((unsigned)d.L[0], (unsigned)P, 1, (unsigned)d.L[0]);
-    X.lx = make_lines((unsigned)(nfc * d.L[1]));
-    X.ly = make_lines((unsigned)(nfc * d.L[0]));
-    X.nfc = nfc;
-    sh->zt = Z;
+    sh->xw = xw;
     return true;
 }
 
-// default shape: the largest scratch and pencil width up to the preferred ones that fit
-bool pick_shape(const Lat& d, size_t elem, int prefer_nfc, int prefer_xw, Shape* sh)
+// default shape: the widest pencil up to the preferred width that fits
+bool pick_shape(const Lat& d, size_t elem, int prefer_xw, Shape* sh)
 {
-    for (int nfc = prefer_nfc; nfc >= 1; nfc >>= 1)
-        for (int xw = prefer_xw; xw >= 1; xw >>= 1)
-            if (make_shape(d, elem, 512, nfc, 512, xw, sh)) return true;
+    for (int xw = prefer_xw; xw >= 1; xw >>= 1)
+        if (make_shape(d, elem, 128, 128, xw, sh)) return true;
     return false;
 }
 
@@ -403,8 +391,8 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     d.ne = (flags & LGF_LINKS18) ? 9 : (flags & LGF_LINKS8) ? 4 : 6;
     c->lat32 = d;
     c->lat32.ne = 6;
-    if (!pick_shape(d, sizeof(double2), 2, 4, &c->sh64)) return LGF_ERR_UNSUPPORTED_DIMS;
-    if (!pick_shape(d, sizeof(float2), 2, 8, &c->sh32)) return LGF_ERR_UNSUPPORTED_DIMS;
+    if (!pick_shape(d, sizeof(double2), 4, &c->sh64)) return LGF_ERR_UNSUPPORTED_DIMS;
+    if (!pick_shape(d, sizeof(float2), 8, &c->sh32)) return LGF_ERR_UNSUPPORTED_DIMS;
 
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
@@ -584,29 +572,27 @@ template <typename T> int autotune_prec(lgf_ctx* c)
     }
     Shape best = shape_ref<T>(c);
     float best_xy = 1e30f, best_zt = 1e30f;
-    const int nts[2] = {256, 512};
-    for (int nt : nts)
-        for (int nfc = 1; nfc <= 4; nfc <<= 1) {
-            Shape cand;
-            if (!make_shape(lat_of<T>(c), elem, nt, nfc, best.nt_zt, best.zt.xw, &cand)) continue;
-            float ms;
-            CKR(time_shape<T>(c, cand, 0, &ms));
-            if (ms < best_xy) {
-                best_xy = ms;
-                best.nt_xy = cand.nt_xy;
-                best.xy = cand.xy;
-            }
+    const int nts[3] = {64, 128, 256};
+    for (int nt : nts) {
+        Shape cand;
+        if (!make_shape(lat_of<T>(c), elem, nt, best.nt_zt, best.xw, &cand)) continue;
+        float ms;
+        CKR(time_shape<T>(c, cand, 0, &ms));
+        if (ms < best_xy) {
+            best_xy = ms;
+            best.nt_xy = cand.nt_xy;
         }
+    }
     for (int nt : nts)
         for (int xw = 1; xw <= 16; xw <<= 1) {
             Shape cand;
-            if (!make_shape(lat_of<T>(c), elem, best.nt_xy, best.xy.nfc, nt, xw, &cand)) continue;
+            if (!make_shape(lat_of<T>(c), elem, best.nt_xy, nt, xw, &cand)) continue;
             float ms;
             CKR(time_shape<T>(c, cand, 1, &ms));
             if (ms < best_zt) {
                 best_zt = ms;
                 best.nt_zt = cand.nt_zt;
-                best.zt = cand.zt;
+                best.xw = cand.xw;
             }
         }
     shape_ref<T>(c) = best;

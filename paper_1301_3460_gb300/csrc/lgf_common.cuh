@@ -22,23 +22,23 @@ template <typename T> struct cx {
     T re, im;
 };
 
-template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { return cx<T>{r, i}; }
-template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
-template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
-template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, T s) { return {a.re * s, a.im * s}; }
-template <typename T> __device__ __forceinline__ cx<T> conjg(cx<T> a) { return {a.re, -a.im}; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T r, T i) { return cx<T>{r, i}; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, T s) { return {a.re * s, a.im * s}; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> conjg(cx<T> a) { return {a.re, -a.im}; }
 // a * b
-template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
 {
     return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
 }
 // a * conj(b)
-template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b)
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b)
 {
     return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -a.re * b.im)};
 }
 // acc + a * b
-template <typename T> __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b)
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b)
 {
     acc.re = fma(a.re, b.re, acc.re);
     acc.re = fma(-a.im, b.im, acc.re);
@@ -47,7 +47,7 @@ template <typename T> __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, 
     return acc;
 }
 // acc + a * conj(b)
-template <typename T> __device__ __forceinline__ cx<T> cmacc(cx<T> acc, cx<T> a, cx<T> b)
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmacc(cx<T> acc, cx<T> a, cx<T> b)
 {
     acc.re = fma(a.re, b.re, acc.re);
     acc.re = fma(a.im, b.im, acc.re);
@@ -56,9 +56,9 @@ template <typename T> __device__ __forceinline__ cx<T> cmacc(cx<T> acc, cx<T> a,
     return acc;
 }
 // -i * a and +i * a
-template <typename T> __device__ __forceinline__ cx<T> mul_mi(cx<T> a) { return {a.im, -a.re}; }
-template <typename T> __device__ __forceinline__ cx<T> mul_pi(cx<T> a) { return {-a.im, a.re}; }
-template <typename T> __device__ __forceinline__ T norm2(cx<T> a) { return fma(a.re, a.re, a.im * a.im); }
+template <typename T> __host__ __device__ __forceinline__ cx<T> mul_mi(cx<T> a) { return {a.im, -a.re}; }
+template <typename T> __host__ __device__ __forceinline__ cx<T> mul_pi(cx<T> a) { return {-a.im, a.re}; }
+template <typename T> __host__ __device__ __forceinline__ T norm2(cx<T> a) { return fma(a.re, a.re, a.im * a.im); }
 
 template <typename T> __device__ __forceinline__ cx<T> ld(const vec2_t<T>* p)
 {
@@ -81,7 +81,7 @@ template <typename T> __device__ __forceinline__ void st(vec2_t<T>* p, cx<T> a)
 // ---------------------------------------------------------------- SU(3)
 
 // conj(a b - c d) with four fused multiply-adds per component
-template <typename T> __device__ __forceinline__ cx<T> cdet2c(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
+template <typename T> __host__ __device__ __forceinline__ cx<T> cdet2c(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
 {
     T re = a.re * b.re;
     re = fma(-a.im, b.im, re);
@@ -96,7 +96,7 @@ template <typename T> __device__ __forceinline__ cx<T> cdet2c(cx<T> a, cx<T> b, 
 
 // third row of an SU(3) matrix from its first two (m[0..2] row 0, m[3..5] row 1):
 // r2 = conj(r0 x r1)
-template <typename T> __device__ __forceinline__ void complete_row2(const cx<T>* m, cx<T>* r2)
+template <typename T> __host__ __device__ __forceinline__ void complete_row2(const cx<T>* m, cx<T>* r2)
 {
     r2[0] = cdet2c(m[1], m[5], m[2], m[4]);
     r2[1] = cdet2c(m[2], m[3], m[0], m[5]);

@@ -7,6 +7,9 @@ namespace lgf {
 
 LGF_INSTANTIATE(double)
 
+size_t plane_tile_bytes(const Lat& d, size_t elem) { return plane_smem_bytes(d, elem); }
+size_t pencil_tile_bytes(const Lat& d, int xw, size_t elem) { return pencil_smem_bytes(d, xw, elem); }
+
 namespace {
 inline unsigned blocks(long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 }  // namespace

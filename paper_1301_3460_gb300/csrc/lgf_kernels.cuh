@@ -23,11 +23,138 @@
 // it maps each packed real pair to a real pair and the packing commutes with it.
 #pragma once
 #include "lgf_common.cuh"
-#include "lgf_fft.cuh"
+#include "lgf_dft.cuh"
 
 namespace lgf {
 
 __device__ __forceinline__ int ld_flag(const int* p) { return *(const volatile int*)p; }
+
+// ---------------------------------------------------------------- tiles and line passes
+
+// Occupancy floor of the tiled FFT kernels: FP32 kernels (bound by memory
+// latency) keep two blocks of 256 threads per SM, FP64 kernels (bound by the
+// FP64 pipe, which a few warps keep busy) may use every register.
+template <typename T> constexpr int kTileMinBlocks = sizeof(T) == 4 ? 2 : 1;
+
+// Shared-memory tiles.  The xy-plane tile holds the four fields of one plane as
+// [f][y][x] with row stride Lx + 1 (odd, so that the rows of consecutive lanes
+// start in different banks) and field stride Ly (Lx + 1).  The z,t pencil tile
+// of xw x-columns holds [t][kz][xi] with row stride rs = Lz xw, padded by xw when
+// xw is narrower than one shared-memory wavefront (then consecutive t fall in
+// different banks), followed by the pencil's multipliers [kt][kz][xi].
+__host__ __device__ inline int plane_rsx(const Lat& d) { return d.L[0] + 1; }
+__host__ __device__ inline int plane_fs(const Lat& d) { return d.L[1] * (d.L[0] + 1); }
+__host__ __device__ inline size_t plane_smem_bytes(const Lat& d, size_t elem) { return 4 * (size_t)plane_fs(d) * elem; }
+__host__ __device__ inline int pencil_rs(const Lat& d, int xw, size_t elem)
+{
+    return (xw * (int)elem < 128 ? d.L[2] + 1 : d.L[2]) * xw;
+}
+// the pencil tile and, after it, the pencil's multipliers (xw Lz Lt reals of elem/2 bytes)
+__host__ __device__ inline size_t pencil_smem_bytes(const Lat& d, int xw, size_t elem)
+{
+    return (size_t)d.L[3] * pencil_rs(d, xw, elem) * elem + (size_t)xw * d.L[2] * d.L[3] * (elem / 2);
+}
+
+// Transform nlines lines of length L (forward, or inverse when INV): each line
+// is read through ld(line, position) and written through st(line, position,
+// value), positions 0..L-1 along the line in natural order (time in, frequency
+// out for the forward transform; the reverse for the inverse).  The lanes of a
+// line (line_lanes(L) of them) work together, so every thread of the block
+// calls this with the same nlines; lines are dealt out a warp at a time.
+template <typename T, int L, bool INV, typename LD, typename ST>
+__device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st, const vec2_t<T>* __restrict__ tw)
+{
+    constexpr int Tl = line_lanes<T>(L), R = L / Tl, W = 32 / Tl;
+    const int lane = (int)threadIdx.x & 31, tau = lane / W, w = lane - tau * W;
+    const int step = ((int)blockDim.x >> 5) * W;
+    for (int l0 = ((int)threadIdx.x >> 5) * W; l0 < nlines; l0 += step) {
+        const int l = l0 + w;
+        const bool ok = l < nlines;
+        const int lc = ok ? l : l0;
+        cx<T> v[R];
+#pragma unroll
+        for (int j = 0; j < R; j++) v[j] = ld(lc, INV ? line_pos_k<T, L>(tau, j) : line_pos_x<T, L>(tau, j));
+        if constexpr (INV) line_inv<T, L>(v, tau, tw);
+        else line_fwd<T, L>(v, tau, tw);
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < R; j++) st(l, INV ? line_pos_x<T, L>(tau, j) : line_pos_k<T, L>(tau, j), v[j]);
+        }
+    }
+}
+
+// Forward transform, a real multiplier per frequency m(line, k), inverse
+// transform, in one pass over the lines (natural order in and out).
+template <typename T, int L, typename LD, typename MUL, typename ST>
+__device__ __forceinline__ void lines_accel(int nlines, LD ld, MUL mul, ST st, const vec2_t<T>* __restrict__ tw)
+{
+    constexpr int Tl = line_lanes<T>(L), R = L / Tl, W = 32 / Tl;
+    const int lane = (int)threadIdx.x & 31, tau = lane / W, w = lane - tau * W;
+    const int step = ((int)blockDim.x >> 5) * W;
+    for (int l0 = ((int)threadIdx.x >> 5) * W; l0 < nlines; l0 += step) {
+        const int l = l0 + w;
+        const bool ok = l < nlines;
+        const int lc = ok ? l : l0;
+        cx<T> v[R];
+#pragma unroll
+        for (int j = 0; j < R; j++) v[j] = ld(lc, line_pos_x<T, L>(tau, j));
+        line_fwd<T, L>(v, tau, tw);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const T m = mul(lc, line_pos_k<T, L>(tau, r));
+            v[r].re *= m;
+            v[r].im *= m;
+        }
+        line_inv<T, L>(v, tau, tw);
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < R; j++) st(l, line_pos_x<T, L>(tau, j), v[j]);
+        }
+    }
+}
+
+// The x-lines (rows) of the four fields of a plane tile, in place.
+template <typename T, bool INV>
+__device__ __forceinline__ void tile_x_lines(const Lat& d, vec2_t<T>* sm, const vec2_t<T>* __restrict__ tw)
+{
+    const int Ly = d.L[1], rsx = plane_rsx(d), fs = plane_fs(d);
+    with_length(d.L[0], [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        auto row = [&](int l) {
+            const int f = l / Ly, y = l - f * Ly;
+            return sm + f * fs + y * rsx;
+        };
+        lines_pass<T, L, INV>(
+            4 * Ly, [&](int l, int e) { return ldv<T>(row(l) + e); },
+            [&](int l, int e, cx<T> v) { st<T>(row(l) + e, v); }, tw);
+    });
+}
+
+// The y-lines (columns) of the four fields of a plane: loaded from src (the
+// tile, or the plane's fields in global memory, [f][y][x] with field stride
+// src_fs and row stride src_rs), transformed, stored to dst likewise.
+template <typename T, bool INV>
+__device__ __forceinline__ void plane_y_lines(const Lat& d, const vec2_t<T>* src, int src_fs, int src_rs,
+                                              vec2_t<T>* dst, int dst_fs, int dst_rs,
+                                              const vec2_t<T>* __restrict__ tw)
+{
+    // offsets stay 32-bit: four fields of V sites, V < 2^31 / 24
+    const int Lx = d.L[0];
+    with_length(d.L[1], [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        lines_pass<T, L, INV>(
+            4 * Lx,
+            [&](int l, int e) {
+                const int f = l / Lx, x = l - f * Lx;
+                return ldv<T>(src + (f * src_fs + e * src_rs + x));
+            },
+            [&](int l, int e, cx<T> v) {
+                const int f = l / Lx, x = l - f * Lx;
+                st<T>(dst + (f * dst_fs + e * dst_rs + x), v);
+            },
+            tw);
+    });
+}
 
 // ---------------------------------------------------------------- reductions
 
@@ -205,129 +332,143 @@ __global__ void __launch_bounds__(256) k_ah_init(Lat d, const vec2_t<T>* __restr
     Fs[s] = f;
 }
 
-// One block per xy-plane.  Shared memory: (4 + nfc) * P complex values.
-// Delta(x) = sum_mu ah_mu(x - mu) - ah_mu(x) (packed fields), theta and F
-// reduced in FP64, then (FFT = true) the forward FFT along x and y.
+// One block per xy-plane.  Delta(x) = sum_mu ah_mu(x - mu) - ah_mu(x) (packed
+// fields), theta and F reduced in FP64; with FFT, the forward transform along x
+// (rows of the plane tile) and y (columns, stored straight to Fd), else Delta
+// itself to Fd.  Shared memory: the plane tile (FFT only).
 template <typename T, bool FFT>
-__global__ void __launch_bounds__(kMaxThreads) k_delta(Lat d, const XyFft F, const vec2_t<T>* __restrict__ AH,
-                                                       const T* __restrict__ Fs, vec2_t<T>* __restrict__ Fd,
-                                                       double* __restrict__ partials, Ctl* ctl, double2* hist,
-                                                       const vec2_t<T>* __restrict__ twx,
-                                                       const vec2_t<T>* __restrict__ twy)
+__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const vec2_t<T>* __restrict__ AH, const T* __restrict__ Fs,
+                                               vec2_t<T>* __restrict__ Fd, double* __restrict__ partials, Ctl* ctl,
+                                               double2* hist, const vec2_t<T>* __restrict__ twx,
+                                               const vec2_t<T>* __restrict__ twy)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
     if (ld_flag(&ctl->phase_done)) return;
-    const int P = d.P, V = d.V;
+    const int P = d.P, V = d.V, Lx = d.L[0];
     const int plane = blockIdx.x;
     const int s0 = plane * P;
     const int z = plane % d.L[2], t = plane / d.L[2];
+    const int rsx = plane_rsx(d), fs = plane_fs(d);
     double th = 0.0, fsum = 0.0;
-#pragma unroll 4
+#pragma unroll 2
     for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
         const int s = s0 + xy;
-        const int x = xy % d.L[0], y = xy / d.L[0];
+        const int y = xy / Lx, x = xy - y * Lx;
         const int c[4] = {x, y, z, t};
+        int sb[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) sb[mu] = site_shift(d, s, c[mu], mu, -1);
+        // every load of the site issued before the arithmetic
+        cx<T> a[16], b[16];
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                a[4 * mu + k] = ld<T>(AH + (size_t)(mu * 4 + k) * V + sb[mu]);
+                b[4 * mu + k] = ld<T>(AH + (size_t)(mu * 4 + k) * V + s);
+            }
+        fsum += (double)__ldg(Fs + s);
         cx<T> D[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) D[k] = mk<T>(0, 0);
+        for (int k = 0; k < 4; k++) {
+            D[k] = a[k] - b[k];
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            const int sb = site_shift(d, s, c[mu], mu, -1);
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                D[k] = D[k] + ld<T>(AH + (size_t)(mu * 4 + k) * V + sb) - ld<T>(AH + (size_t)(mu * 4 + k) * V + s);
+            for (int mu = 1; mu < 4; mu++) D[k] = D[k] + a[4 * mu + k] - b[4 * mu + k];
         }
-        fsum += (double)__ldg(Fs + s);
-        const T a = D[3].re, b = D[3].im, cc = a + b;
+        const T p = D[3].re, q = D[3].im, pq = p + q;
         // per-site sum of |Delta_ij|^2 in the kernel's precision, accumulated over
         // sites in FP64
-        th += (double)((T)2 * (norm2(D[0]) + norm2(D[1]) + norm2(D[2])) + a * a + b * b + cc * cc);
+        th += (double)((T)2 * (norm2(D[0]) + norm2(D[1]) + norm2(D[2])) + p * p + q * q + pq * pq);
+        if (FFT) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) st<T>(sm + k * P + xy, D[k]);
+            for (int k = 0; k < 4; k++) st<T>(sm + k * fs + y * rsx + x, D[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) st<T>(Fd + (size_t)k * V + s, D[k]);
+        }
     }
     reduce_theta_F(th, fsum, partials, ctl, hist, V);
-    __syncthreads();
-    // forward FFT along x (lines: fields x Ly rows) and along y (fields x Lx columns)
-    if (FFT) fft_xy_fields<T>(F, P, sm, sm + 4 * P, twx, twy, kFwd);
-    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
-        const int f = i / P, xy = i - f * P;
-        Fd[(size_t)f * V + s0 + xy] = sm[i];
+    if (FFT) {
+        __syncthreads();
+        tile_x_lines<T, false>(d, sm, twx);
+        __syncthreads();
+        plane_y_lines<T, false>(d, sm, fs, rsx, Fd + s0, V, Lx, twy);
     }
 }
 
 // ---------------------------------------------------------------- k_zt
 
-// One block per (x-chunk of xw columns, y, field).  Shared memory: two buffers of
-// Lt rows of Z.rs >= xw * Lz values, laid out [t][z][xi].  Data arrive transformed along x and
-// y, so the x and y indices are the momenta kx, ky.
+// One block per (x-chunk of xw columns, y, field); the fields arrive transformed
+// along x and y, so x and y are the momenta kx, ky.  The pencil's multipliers
+// p2max/(p2(k) V) (zero mode removed; mult is the table of them, site-indexed by
+// momentum, never null) are staged in shared memory; z-lines are read from Fd
+// into registers and transformed forward, stored to the pencil tile
+// [t][kz][xi]; each t-line is transformed forward, multiplied by the
+// accelerator and transformed back; the z-lines are transformed back and
+// written to Fd.
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_zt(Lat d, const ZtFft Z, vec2_t<T>* __restrict__ Fd, const Ctl* ctl,
-                                                    const vec2_t<T>* __restrict__ twz,
-                                                    const vec2_t<T>* __restrict__ twt, const T* __restrict__ mult,
-                                                    const double* __restrict__ s2x, const double* __restrict__ s2y,
-                                                    const double* __restrict__ s2z, const double* __restrict__ s2t,
-                                                    double p2max)
+__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_zt(Lat d, int xw, vec2_t<T>* __restrict__ Fd, const Ctl* ctl,
+                                            const vec2_t<T>* __restrict__ twz, const vec2_t<T>* __restrict__ twt,
+                                            const T* __restrict__ mult)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
     if (ld_flag(&ctl->phase_done)) return;
-    const int XW = Z.xw, RS = Z.rs;
-    const int Lz = d.L[2], Lt = d.L[3], P = d.P;
-    const int x0 = blockIdx.x * XW, y = blockIdx.y, f = blockIdx.z;
-    vec2_t<T>* base = Fd + (size_t)f * d.V + x0 + d.L[0] * y;
-    const int n = XW * Lz * Lt;
-    const int LzXW = Lz * XW;
-    // value i = xi + XW (z + Lz t) of the pencil sits at t RS + (i mod Lz XW) in the tile
-#pragma unroll 4
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int zt = i / XW, xi = i - zt * XW;
-        const int t = i / LzXW;
-        sm[i + t * (RS - LzXW)] = base[xi + (size_t)P * zt];
-    }
-    __syncthreads();
-    vec2_t<T>* a = sm;
-    vec2_t<T>* b = sm + (size_t)Lt * RS;
-    // forward along z and t
-    vec2_t<T>* r = fft_lines<T>(Z.pz, a, b, Z.lz, 1, Z.mz, twz, kFwd);
-    r = fft_lines<T>(Z.pt, r, r == a ? b : a, Z.lt, 1, Z.mt, twt, kFwd);
-    // the accelerator p2max / (p2(k) V), zero mode removed: from the table of
-    // multipliers (site-indexed by momentum) when there is one, else computed
-    if (mult != nullptr) {
-        const T* mrow = mult + x0 + d.L[0] * y;
-#pragma unroll 4
+    const int Lz = d.L[2], Lt = d.L[3];
+    const int P = d.P;  // offsets stay 32-bit (V < 2^31 / 24)
+    const int rs = pencil_rs(d, xw, sizeof(vec2_t<T>));
+    const int c0 = (int)blockIdx.x * xw + d.L[0] * (int)blockIdx.y;  // (kx0, ky)
+    vec2_t<T>* g = Fd + (size_t)blockIdx.z * d.V + c0;
+    T* msm = reinterpret_cast<T*>(sm + Lt * rs);
+    {
+        const int n = xw * Lz * Lt;
+        const T* mrow = mult + c0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int zt = i / XW, xi = i - zt * XW;
-            const int o = i + (i / LzXW) * (RS - LzXW);
-            const T m = __ldg(mrow + xi + (size_t)P * zt);
-            vec2_t<T> v = r[o];
-            v.x *= m;
-            v.y *= m;
-            r[o] = v;
-        }
-    } else {
-        const double inv_v = 1.0 / (double)d.V;
-        const double sy = s2y[y];
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int zt = i / XW, xi = i - zt * XW;
-            const int kt = zt / Lz, kz = zt - kt * Lz;
-            const double p2 = s2x[x0 + xi] + sy + s2z[kz] + s2t[kt];
-            const T m = (p2 > 0.0) ? (T)(p2max / p2 * inv_v) : (T)0;
-            const int o = i + kt * (RS - LzXW);
-            vec2_t<T> v = r[o];
-            v.x *= m;
-            v.y *= m;
-            r[o] = v;
+            const int zt = i / xw, xi = i - zt * xw;
+            msm[i] = __ldg(mrow + (xi + P * zt));
         }
     }
+    // z forward: lines (xi, t)
+    with_length(Lz, [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        lines_pass<T, L, false>(
+            xw * Lt,
+            [&](int l, int e) {
+                const int tt = l / xw, xi = l - tt * xw;
+                return ldv<T>(g + (xi + P * (e + L * tt)));
+            },
+            [&](int l, int e, cx<T> v) {
+                const int tt = l / xw, xi = l - tt * xw;
+                st<T>(sm + tt * rs + e * xw + xi, v);
+            },
+            twz);
+    });
     __syncthreads();
-    // inverse along t and z
-    r = fft_lines<T>(Z.pt, r, r == a ? b : a, Z.lt, 1, Z.mt, twt, kInv);
-    r = fft_lines<T>(Z.pz, r, r == a ? b : a, Z.lz, 1, Z.mz, twz, kInv);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int zt = i / XW, xi = i - zt * XW;
-        base[xi + (size_t)P * zt] = r[i + (i / LzXW) * (RS - LzXW)];
-    }
+    // t forward, accelerator, t inverse: lines (xi, kz)
+    with_length(Lt, [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        lines_accel<T, L>(
+            xw * Lz, [&](int l, int e) { return ldv<T>(sm + e * rs + l); },
+            [&](int l, int k) { return msm[l + xw * Lz * k]; },
+            [&](int l, int e, cx<T> v) { st<T>(sm + e * rs + l, v); }, twt);
+    });
+    __syncthreads();
+    // z inverse: lines (xi, t), back to Fd
+    with_length(Lz, [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        lines_pass<T, L, true>(
+            xw * Lt,
+            [&](int l, int e) {
+                const int tt = l / xw, xi = l - tt * xw;
+                return ldv<T>(sm + tt * rs + e * xw + xi);
+            },
+            [&](int l, int e, cx<T> v) {
+                const int tt = l / xw, xi = l - tt * xw;
+                st<T>(g + (xi + P * (e + L * tt)), v);
+            },
+            twz);
+    });
 }
 
 // multiplier table p2max / (p2(k) V) for every momentum k (site-indexed), FP64 and FP32
@@ -391,28 +532,30 @@ __device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>
     complete_row2(g, g + 6);
 }
 
-// One block per xy-plane.  g is built in FP64 whatever T is, and stored as TG.
+// One block per xy-plane: inverse transform along y (columns read from Fd) and x
+// (rows of the plane tile), then g = reunit(1 + alpha/2 Delta~) by row
+// Gram-Schmidt in FP64 whatever T is; g stored as TG.
 template <typename T, typename TG>
-__global__ void __launch_bounds__(kMaxThreads) k_xyinv_g(Lat d, const XyFft F, const vec2_t<T>* __restrict__ Fd,
-                                                         vec2_t<TG>* __restrict__ g,
-                                                const Ctl* ctl, const vec2_t<T>* __restrict__ twx,
-                                                const vec2_t<T>* __restrict__ twy)
+__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
+                                                 vec2_t<TG>* __restrict__ g, const Ctl* ctl,
+                                                 const vec2_t<T>* __restrict__ twx,
+                                                 const vec2_t<T>* __restrict__ twy)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
     if (ld_flag(&ctl->phase_done)) return;
-    const int P = d.P, V = d.V;
+    const int P = d.P, V = d.V, Lx = d.L[0];
     const int s0 = blockIdx.x * P;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
-        const int f = i / P, xy = i - f * P;
-        sm[i] = Fd[(size_t)f * V + s0 + xy];
-    }
+    const int rsx = plane_rsx(d), fs = plane_fs(d);
+    plane_y_lines<T, true>(d, Fd + s0, V, Lx, sm, fs, rsx, twy);
     __syncthreads();
-    fft_xy_fields<T>(F, P, sm, sm + 4 * P, twx, twy, kInv);
+    tile_x_lines<T, true>(d, sm, twx);
+    __syncthreads();
     const double h = 0.5 * ctl->alpha;
     for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
-        vec2_t<T> f0 = sm[xy], f1 = sm[P + xy], f2 = sm[2 * P + xy], f3 = sm[3 * P + xy];
+        const int y = xy / Lx, x = xy - y * Lx;
+        const int o = y * rsx + x;
+        vec2_t<T> f0 = sm[o], f1 = sm[fs + o], f2 = sm[2 * fs + o], f3 = sm[3 * fs + o];
         // X = 1 + (alpha/2) Delta~ ; rows 0 and 1
         cx<double> X[6];
         X[0] = mk<double>(1.0, h * (double)f3.x);

@@ -6,7 +6,6 @@
 #include <cuda_runtime.h>
 
 #include "lgf_common.cuh"
-#include "lgf_fft.cuh"
 
 namespace lgf {
 
@@ -20,13 +19,18 @@ struct Tables {
     const float* mult32;
 };
 
-// launch shape and FFT plans of the plane-tiled kernels of one precision
+// launch shape of the tiled FFT kernels of one precision
 struct Shape {
-    int nt_xy;   // threads of the xy-plane kernels
-    int nt_zt;   // threads of the zt-pencil kernel
-    XyFft xy;    // x and y transforms, chunks of nfc fields
-    ZtFft zt;    // z and t transforms of pencils of xw columns
+    int nt_xy;   // threads of the xy-plane kernels (a multiple of 32, at most 256)
+    int nt_zt;   // threads of the zt-pencil kernel (likewise)
+    int xw;      // x-columns per zt pencil (divides Lx)
 };
+
+// shared memory of the plane tile and of one pencil (element size elem)
+size_t plane_tile_bytes(const Lat& d, size_t elem);
+size_t pencil_tile_bytes(const Lat& d, int xw, size_t elem);
+// shared-memory budget of one tile; extents whose tiles exceed it are refused
+constexpr size_t kTileBudget = 220 * 1024;
 
 template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh);
 template <typename T>

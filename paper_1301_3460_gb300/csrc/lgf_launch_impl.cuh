@@ -5,7 +5,6 @@
 
 #include "lgf_aux.cuh"
 #include "lgf_launch.h"
-#include "lgf_zt_lines.cuh"
 
 namespace lgf {
 
@@ -17,13 +16,10 @@ template <typename T> inline const vec2_t<T>* tw_of(const Tables& tb, int mu);
 template <> inline const double2* tw_of<double>(const Tables& tb, int mu) { return tb.tw64[mu]; }
 template <> inline const float2* tw_of<float>(const Tables& tb, int mu) { return tb.tw32[mu]; }
 
-template <typename T> inline size_t xy_smem(const Lat& d, const Shape& sh)
-{
-    return (size_t)(4 + sh.xy.nfc) * d.P * sizeof(vec2_t<T>);
-}
+template <typename T> inline size_t xy_smem(const Lat& d) { return plane_smem_bytes(d, sizeof(vec2_t<T>)); }
 template <typename T> inline size_t zt_smem(const Lat& d, const Shape& sh)
 {
-    return zt_tile_bytes(sh.zt, d.L[3], sizeof(vec2_t<T>));
+    return pencil_smem_bytes(d, sh.xw, sizeof(vec2_t<T>));
 }
 
 template <typename K> inline cudaError_t allow_max_smem(K* kernel, int optin)
@@ -44,21 +40,12 @@ template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh)
     cudaError_t e;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
-    if ((size_t)optin < xy_smem<T>(d, sh) + 1024 || (size_t)optin < zt_smem<T>(d, sh)) return cudaErrorInvalidValue;
+    if ((size_t)optin < xy_smem<T>(d) + 1024 || (size_t)optin < zt_smem<T>(d, sh)) return cudaErrorInvalidValue;
     if ((e = allow_max_smem(k_delta<T, true>, optin))) return e;
     if ((e = allow_max_smem(k_delta<T, false>, optin))) return e;
     if ((e = allow_max_smem(k_xyinv_g<T, T>, optin))) return e;
     if ((e = allow_max_smem(k_xy_fft<T, false>, optin))) return e;
     if ((e = allow_max_smem(k_xy_fft<T, true>, optin))) return e;
-    if constexpr (std::is_same<T, float>::value) {
-        const void* lines[] = {(const void*)k_zt_lines<8, 4>,  (const void*)k_zt_lines<8, 8>,
-                               (const void*)k_zt_lines<8, 16>, (const void*)k_zt_lines<16, 4>,
-                               (const void*)k_zt_lines<16, 8>, (const void*)k_zt_lines<16, 16>,
-                               (const void*)k_zt_lines<32, 4>, (const void*)k_zt_lines<32, 8>,
-                               (const void*)k_zt_lines<32, 16>};
-        for (const void* k : lines)
-            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin))) return e;
-    }
     return allow_max_smem(k_zt<T>, optin);
 }
 
@@ -66,13 +53,12 @@ template <typename T>
 void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* AH, const T* Fs,
                   vec2_t<T>* Fd, double* partials, Ctl* ctl, double2* hist, bool fft)
 {
-    const size_t sm = xy_smem<T>(d, sh);
     if (fft)
-        k_delta<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, AH, Fs, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
-                                                         tw_of<T>(tb, 1));
+        k_delta<T, true><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist,
+                                                                    tw_of<T>(tb, 0), tw_of<T>(tb, 1));
     else
-        k_delta<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, AH, Fs, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
-                                                          tw_of<T>(tb, 1));
+        k_delta<T, false><<<d.nplanes, sh.nt_xy, 0, s>>>(d, AH, Fs, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
+                                                         tw_of<T>(tb, 1));
 }
 
 template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const vec2_t<T>* U, vec2_t<T>* AH, T* Fs)
@@ -83,26 +69,16 @@ template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const ve
 template <typename T>
 void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl)
 {
-    dim3 grid(d.L[0] / sh.zt.xw, d.L[1], 4);
-    if constexpr (std::is_same<T, float>::value) {
-        // FP32 phase, Lz = Lt <= 32: whole lines in registers
-        const int n = zt_lines_n(d, sh.zt.xw);
-        if (n != 0 && tb.mult32 != nullptr) {
-            launch_zt_lines(n, sh.zt.xw, s, d, Fd, ctl, tb.mult32);
-            return;
-        }
-    }
-    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.zt, Fd, ctl, tw_of<T>(tb, 2), tw_of<T>(tb, 3),
-                                                      mult_of<T>(tb), tb.s2[0], tb.s2[1], tb.s2[2], tb.s2[3],
-                                                      tb.p2max);
+    const dim3 grid(d.L[0] / sh.xw, d.L[1], 4);
+    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tw_of<T>(tb, 2), tw_of<T>(tb, 3),
+                                                      mult_of<T>(tb));
 }
 
 template <typename T>
 void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* Fd,
                     vec2_t<T>* g, const Ctl* ctl)
 {
-    k_xyinv_g<T, T><<<d.nplanes, sh.nt_xy, xy_smem<T>(d, sh), s>>>(d, sh.xy, Fd, g, ctl, tw_of<T>(tb, 0),
-                                                                   tw_of<T>(tb, 1));
+    k_xyinv_g<T, T><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
 }
 
 template <typename T> void launch_build_g(const Lat& d, cudaStream_t s, const vec2_t<T>* Fd, vec2_t<T>* g, const Ctl* ctl)
@@ -113,11 +89,11 @@ template <typename T> void launch_build_g(const Lat& d, cudaStream_t s, const ve
 template <typename T>
 void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, bool inv)
 {
-    const size_t sm = xy_smem<T>(d, sh);
+    const size_t sm = xy_smem<T>(d);
     if (inv)
-        k_xy_fft<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+        k_xy_fft<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
     else
-        k_xy_fft<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, sh.xy, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+        k_xy_fft<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
 }
 
 template <typename T>

@@ -6,13 +6,14 @@
 // nothing left to give a library that calls cudaMalloc; lgf_create allocates a
 // context, so they cannot use lgf_accelerate.  This entry point runs the same
 // kernels with its scratch (the four packed colour fields, the twiddle and
-// momentum tables and the small control block) in a file-scope device array,
-// so the call itself allocates nothing: the caller passes only the input and
-// output buffers.
+// momentum tables, the accelerator's multiplier table and the small control
+// block) in a file-scope device array, so the call itself allocates nothing:
+// the caller passes only the input and output buffers.
 //
-// The array is sized for lattices of up to kMaxSites sites (4 MiB of fields plus
-// tables), is part of the loaded module and is therefore held on every GPU that
-// loads the library until the process exits.  All calls share it and it keeps
+// The array is sized for lattices of up to kMaxSites sites (4 MiB of fields,
+// 0.75 MiB of multipliers and the small tables), is part of the loaded module
+// and is therefore held on every GPU that loads the library until the process
+// exits.  All calls share it and it keeps
 // the last call's contents; the control block is cleared on every call and the
 // fields and tables are overwritten before use.  Two calls whose work overlaps
 // on the GPU (different streams, or different host threads on one device) race
@@ -29,6 +30,7 @@
 #include <mutex>
 
 #include "../../include/lgf.h"
+#include "lgf_dft.cuh"
 #include "lgf_launch.h"
 
 using namespace lgf;
@@ -41,19 +43,17 @@ constexpr size_t kFieldBytes = (size_t)4 * kMaxSites * sizeof(double2);
 constexpr size_t kTw64Bytes = (size_t)4 * kMaxLen * sizeof(double2);
 constexpr size_t kTw32Bytes = (size_t)4 * kMaxLen * sizeof(float2);
 constexpr size_t kS2Bytes = (size_t)4 * kMaxLen * sizeof(double);
+constexpr size_t kMultBytes = (size_t)kMaxSites * (sizeof(double) + sizeof(float));  // accelerator table, FP64 + FP32
 constexpr size_t kTablesOff = kFieldBytes;
-constexpr size_t kCtlOff = (kTablesOff + kTw64Bytes + kTw32Bytes + kS2Bytes + 255) / 256 * 256;
+constexpr size_t kMultOff = (kTablesOff + kTw64Bytes + kTw32Bytes + kS2Bytes + 255) / 256 * 256;
+constexpr size_t kCtlOff = (kMultOff + kMultBytes + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kCtlOff + (sizeof(Ctl) + 255) / 256 * 256;
 constexpr int kMaxDevices = 64;
 
 std::mutex g_setup_mutex;
 unsigned char* g_scratch[kMaxDevices] = {};  // device address at the last set-up, per device
 
-bool length_ok(int L)
-{
-    return L == 4 || L == 6 || L == 8 || L == 12 || L == 16 || L == 24 || L == 32 || L == 48 || L == 64 ||
-           L == 96 || L == 128;
-}
+bool length_ok(int L) { return line_length_ok(L); }
 
 }  // namespace
 
@@ -79,27 +79,15 @@ extern "C" int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in,
     d.V = (int)V;
     d.P = dims[0] * dims[1];
     d.nplanes = dims[2] * dims[3];
-    // FFT tiles in shared memory: the four fields of an xy-plane plus one field
-    // of scratch, and two buffers of a pencil of up to four x-columns
-    const size_t budget = 220 * 1024;
-    if ((size_t)5 * d.P * sizeof(double2) > budget) return LGF_ERR_UNSUPPORTED_DIMS;
+    // FFT tiles in shared memory: the four fields of an xy-plane, and one z,t
+    // pencil of up to four x-columns
+    if (plane_tile_bytes(d, sizeof(double2)) > kTileBudget) return LGF_ERR_UNSUPPORTED_DIMS;
     Shape sh{};
-    sh.nt_xy = 512;
-    sh.nt_zt = 512;
-    sh.xy.px = make_axis_plan(dims[0]);
-    sh.xy.py = make_axis_plan(dims[1]);
-    sh.xy.mx = make_linemap(1u << 30, 0, (unsigned)dims[0], 1);
-    sh.xy.my = make_linemap((unsigned)dims[0], (unsigned)d.P, 1, (unsigned)dims[0]);
-    sh.xy.nfc = 1;
-    sh.xy.lx = make_lines((unsigned)dims[1]);
-    sh.xy.ly = make_lines((unsigned)dims[0]);
-    int xw = 4;
-    while (xw > 1 && (dims[0] % xw ||
-                      zt_tile_bytes(make_zt_fft(dims[2], dims[3], xw, sizeof(double2)), dims[3], sizeof(double2)) >
-                          budget))
-        xw >>= 1;
-    sh.zt = make_zt_fft(dims[2], dims[3], xw, sizeof(double2));
-    if (zt_tile_bytes(sh.zt, dims[3], sizeof(double2)) > budget) return LGF_ERR_UNSUPPORTED_DIMS;
+    sh.nt_xy = 128;
+    sh.nt_zt = 128;
+    sh.xw = 4;
+    while (sh.xw > 1 && (dims[0] % sh.xw || pencil_tile_bytes(d, sh.xw, sizeof(double2)) > kTileBudget)) sh.xw >>= 1;
+    if (pencil_tile_bytes(d, sh.xw, sizeof(double2)) > kTileBudget) return LGF_ERR_UNSUPPORTED_DIMS;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LGF_ERR_CUDA;
@@ -150,11 +138,16 @@ extern "C" int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     double2* Fd = reinterpret_cast<double2*>(base);
     Ctl* ctl = reinterpret_cast<Ctl*>(base + kCtlOff);
+    double* m64 = reinterpret_cast<double*>(base + kMultOff);
+    float* m32 = reinterpret_cast<float*>(base + kMultOff + (size_t)kMaxSites * sizeof(double));
     if (cudaMemcpyAsync(dtw64, tw64, off * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(dtw32, tw32, off * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(ds2, s2, off * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess)
         return LGF_ERR_CUDA;
+    launch_make_mult(s, d, tb, m64, m32);  // the accelerator's multiplier per momentum
+    tb.mult64 = m64;
+    tb.mult32 = m32;
     launch_pack_delta(s, d.V, Delta_in, Fd);
     launch_xy_fft<double>(d, sh, tb, s, Fd, false);
     launch_zt<double>(d, sh, tb, s, Fd, ctl);

@@ -29,11 +29,11 @@ def no_gpu():
 
 
 def documented_ok(L):
-    """The header's rule: every extent in LENGTHS, Lx*Ly <= 2816,
-    Lt*(Lz + 1) <= 7040, and 24 V within a signed 32-bit offset."""
+    """The header's rule: every extent in LENGTHS, Ly*(Lx + 1) <= 3520,
+    Lt*(3 Lz + 2) <= 28160, and 24 V within a signed 32-bit offset."""
     Lx, Ly, Lz, Lt = L
     V = Lx * Ly * Lz * Lt
-    return Lx * Ly <= 2816 and Lt * (Lz + 1) <= 7040 and 24 * V <= 2**31 - 1
+    return Ly * (Lx + 1) <= 3520 and Lt * (3 * Lz + 2) <= 28160 and 24 * V <= 2**31 - 1
 
 
 def test_every_supported_extent_combination():

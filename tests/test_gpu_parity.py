@@ -278,10 +278,11 @@ def test_pinned_host_buffers_match_pageable():
 
 
 # every FFT length the kernels take, along each axis, on thin lattices the oracle runs in
-# seconds; the last two are the largest planes and pencils the FP64 tiles hold
-# (Lx Ly = 2304 of at most 2816, Lt (Lz + 1) = 6240 of at most 7040)
+# seconds; the last four are the largest planes and pencils the FP64 tiles hold
+# (Ly (Lx + 1) = 3096 and 3120 of at most 3520, Lt (3 Lz + 2) = 27840 and 24832 of
+# at most 28160)
 LONG_AXES = [(128, 4, 4, 4), (4, 96, 4, 4), (4, 4, 64, 4), (4, 4, 4, 128), (48, 6, 4, 4), (4, 4, 24, 48),
-             (16, 4, 96, 4), (96, 24, 4, 4), (4, 4, 64, 96)]
+             (16, 4, 96, 4), (128, 24, 4, 4), (64, 48, 4, 4), (4, 4, 96, 96), (4, 4, 64, 128)]
 
 
 @pytest.mark.parametrize("L", LONG_AXES)
@@ -299,7 +300,7 @@ def test_long_axes_links_after_steps(L):
 
 
 def test_over_the_plane_limits_is_refused():
-    for L in [(128, 32, 4, 4), (128, 24, 4, 4), (4, 4, 128, 128), (4, 4, 128, 96)]:
+    for L in [(128, 32, 4, 4), (64, 64, 4, 4), (96, 48, 4, 4), (4, 4, 128, 128), (4, 4, 96, 128)]:
         with pytest.raises(lgf.LgfError) as e:
             lgf.Lattice(L)
         assert e.value.status == lgf.LGF_ERR_UNSUPPORTED_DIMS
