@@ -923,15 +923,21 @@ def run_kernels(args, dims):
         lat.set_links(U)
         if not args.no_autotune:
             lat.autotune()
-        for prec in (64, 32):
+        # FP64, FP32 with the update fused with Delta (the default), FP32 in the
+        # two-kernel form
+        for name, prec, fused in (("fp64", 64, True), ("fp32", 32, True), ("fp32_unfused", 32, False)):
+            lat.set_fp32_update(fused)
+            if fused is False and not args.no_autotune:
+                lat.autotune()
             if args.warmup:
                 lat.time_kernels(args.alpha, n_iter=args.warmup, precision=prec)
             ms = lat.time_kernels(args.alpha, n_iter=max(1, args.steps), precision=prec)
-            per = roofline.per_site(dims, prec)
-            out["fp%d" % prec] = {k: {"ms": ms[k], "gbs": per[k]["bytes"] * V / ms[k] / 1e6,
-                                      "hbm_frac_of_measured": per[k]["bytes"] * V / ms[k] / 1e6 / hbm,
-                                      "gflops": per[k]["flops"] * V / ms[k] / 1e6} for k in ms}
-            out["fp%d_iteration_ms" % prec] = sum(ms.values())
+            per = roofline.per_site(dims, prec, fused)
+            out[name] = {k: {"ms": ms[k], "gbs": per[k]["bytes"] * V / ms[k] / 1e6,
+                             "hbm_frac_of_measured": per[k]["bytes"] * V / ms[k] / 1e6 / hbm,
+                             "gflops": per[k]["flops"] * V / ms[k] / 1e6} for k in ms}
+            out[name + "_iteration_ms"] = sum(ms.values())
+        lat.set_fp32_update(True)
     print(json.dumps(out), flush=True)
     return 0
 

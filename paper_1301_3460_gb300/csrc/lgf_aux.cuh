@@ -176,9 +176,7 @@ static __global__ void k_unpack_full(int V, const double2* __restrict__ g, doubl
 // plane-wise FFT along x and y of the four fields, in place on Fd (stand-alone
 // stage; one block per xy-plane, the plane tile in shared memory)
 template <typename T, bool INV>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xy_fft(Lat d, vec2_t<T>* __restrict__ Fd,
-                                                const vec2_t<T>* __restrict__ twx,
-                                                const vec2_t<T>* __restrict__ twy)
+__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xy_fft(Lat d, vec2_t<T>* __restrict__ Fd)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
@@ -186,23 +184,35 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xy_fft(Lat d, vec2_t
     const int rsx = plane_rsx(d), fs = plane_fs(d);
     vec2_t<T>* base = Fd + s0;
     if (INV) {
-        plane_y_lines<T, true>(d, base, V, Lx, sm, fs, rsx, twy);
+        plane_y_lines<T, true>(d, base, V, Lx, sm, fs, rsx);
         __syncthreads();
-        tile_x_lines<T, true>(d, sm, twx);
+        tile_x_lines<T, true>(d, sm);
         __syncthreads();
-        for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
-            const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
-            base[(size_t)f * V + xy] = sm[f * fs + y * rsx + x];
-        }
+        block_copy<4, vec2_t<T>>(
+            4 * P,
+            [&](int i) {
+                const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
+                return sm[f * fs + y * rsx + x];
+            },
+            [&](int i, vec2_t<T> v) {
+                const int f = i / P, xy = i - f * P;
+                base[(size_t)f * V + xy] = v;
+            });
     } else {
-        for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
-            const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
-            sm[f * fs + y * rsx + x] = base[(size_t)f * V + xy];
-        }
+        block_copy<8, vec2_t<T>>(
+            4 * P,
+            [&](int i) {
+                const int f = i / P, xy = i - f * P;
+                return base[(size_t)f * V + xy];
+            },
+            [&](int i, vec2_t<T> v) {
+                const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
+                sm[f * fs + y * rsx + x] = v;
+            });
         __syncthreads();
-        tile_x_lines<T, false>(d, sm, twx);
+        tile_x_lines<T, false>(d, sm);
         __syncthreads();
-        plane_y_lines<T, false>(d, sm, fs, rsx, base, V, Lx, twy);
+        plane_y_lines<T, false>(d, sm, fs, rsx, base, V, Lx);
     }
 }
 
@@ -312,7 +322,8 @@ static __global__ void __launch_bounds__(256) k_project(Lat d, double2* __restri
 // whatever the FP32 links had drifted.  Every `every` FP32 updates the links are
 // therefore rebuilt from the input and the (re-orthonormalised) G:
 //   G(x) <- reunit(G(x)),  U32_mu(x) <- G(x) U_in_mu(x) G^dag(x+mu)
-// with the packed anti-Hermitian parts and Re Tr of the new links for Delta.
+// (with the packed anti-Hermitian parts and Re Tr of the new links when AH and
+// Fs are given; the fused FP32 iteration recomputes Delta from the links).
 
 __device__ __forceinline__ bool refresh_due(const Ctl* ctl, int every)
 {
@@ -391,13 +402,15 @@ static __global__ void __launch_bounds__(256) k_refresh_u(Lat d, int ne64, const
                 st<float>(U32 + (size_t)(mu * 6 + 3 * i + j) * V + s, acc);
             }
         complete_row2(w, w + 6);
-        cx<float> a[4];
-        ah_pack(w, a);
+        if (AH != nullptr) {
+            cx<float> a[4];
+            ah_pack(w, a);
 #pragma unroll
-        for (int k = 0; k < 4; k++) st<float>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
+            for (int k = 0; k < 4; k++) st<float>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
+        }
         f += w[0].re + w[4].re + w[8].re;
     }
-    Fs[s] = f;
+    if (Fs != nullptr) Fs[s] = f;
 }
 
 // hand over from the FP32 phase to the FP64 phase

@@ -87,14 +87,16 @@ struct lgf_ctx {
     double2* U64 = nullptr;
     double2* G64 = nullptr;
     double2* g64 = nullptr;   // [9][V]; also the FP64 reprojection of G at the precision switch
-    float2* U32 = nullptr;
+    float2* U32 = nullptr;    // FP32 links of the FP32 phase, and the second buffer the fused
+    float2* U32b = nullptr;   // update writes (the two swap roles every update)
     float2* G32 = nullptr;
     float2* g32 = nullptr;
+    float2* AH32 = nullptr;   // FP32 phase without the fused update: packed anti-Hermitian
+    float* Fs32 = nullptr;    // parts and Re Tr handed from the update to the Delta kernel
+    bool fused32 = true;      // FP32 phase: update fused with Delta (links recomputed) or not
     void* Fd = nullptr;       // [4][V] double2 (the FP32 phase uses the front half as float2)
     double2* AH64 = nullptr;  // [4][4][V] packed anti-Hermitian parts of the links
     double* Fs64 = nullptr;   // [V] Re Tr of the four links of a site
-    float2* AH32 = nullptr;
-    float* Fs32 = nullptr;
     double* partials = nullptr;
     Ctl* ctl = nullptr;       // loop state of lgf_fix
     Ctl* ctl_stage = nullptr; // state used by the stage entry points
@@ -150,12 +152,6 @@ bool pick_shape(const Lat& d, size_t elem, int prefer_xw, Shape* sh)
     return false;
 }
 
-template <typename T> vec2_t<T>* ah_of(lgf_ctx* c);
-template <> double2* ah_of<double>(lgf_ctx* c) { return c->AH64; }
-template <> float2* ah_of<float>(lgf_ctx* c) { return c->AH32; }
-template <typename T> T* fs_of(lgf_ctx* c);
-template <> double* fs_of<double>(lgf_ctx* c) { return c->Fs64; }
-template <> float* fs_of<float>(lgf_ctx* c) { return c->Fs32; }
 
 template <typename T> const Lat& lat_of(const lgf_ctx* c);
 template <> const Lat& lat_of<double>(const lgf_ctx* c) { return c->lat; }
@@ -165,23 +161,63 @@ template <typename T> const Shape& shape_of(const lgf_ctx* c);
 template <> const Shape& shape_of<double>(const lgf_ctx* c) { return c->sh64; }
 template <> const Shape& shape_of<float>(const lgf_ctx* c) { return c->sh32; }
 
-// one iteration after Delta: FFT(z,t)+scale+IFFT(t,z), IFFT(x,y)+g, update, Delta+FFT(x,y)
-template <typename T>
-void launch_body(lgf_ctx* c, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, vec2_t<T>* g)
+// one FP64 iteration after Delta: FFT(z,t)+scale+IFFT(t,z), IFFT(x,y)+g, update,
+// Delta+FFT(x,y)
+void launch_body64(lgf_ctx* c, cudaStream_t s, double2* G)
 {
-    vec2_t<T>* Fd = reinterpret_cast<vec2_t<T>*>(c->Fd);
-    const Shape& sh = shape_of<T>(c);
-    const Lat& d = lat_of<T>(c);
+    double2* Fd = reinterpret_cast<double2*>(c->Fd);
+    const Lat& d = c->lat;
     if (c->plain) {
-        launch_build_g<T>(d, s, Fd, g, c->ctl);
+        launch_build_g<double>(d, s, Fd, c->g64, c->ctl);
     } else {
-        launch_zt<T>(d, sh, c->tb, s, Fd, c->ctl);
-        launch_xyinv_g<T>(d, sh, c->tb, s, Fd, g, c->ctl);
+        launch_zt<double>(d, c->sh64, c->tb, s, Fd, c->ctl);
+        launch_xyinv_g<double>(d, c->sh64, c->tb, s, Fd, c->g64, c->ctl);
     }
-    launch_update<T>(d, s, U, G, g, c->ctl, ah_of<T>(c), fs_of<T>(c));
-    if (sizeof(T) == 4 && c->refresh_every > 0)
-        launch_refresh32(s, c->lat32, c->lat.ne, c->U64, c->G32, c->U32, c->AH32, c->Fs32, c->ctl, c->refresh_every);
-    launch_delta<T>(d, sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl, c->hist, !c->plain);
+    launch_update<double>(d, s, c->U64, G, c->g64, c->ctl, c->AH64, c->Fs64);
+    launch_delta<double>(d, c->sh64, c->tb, s, c->AH64, c->Fs64, Fd, c->partials, c->ctl, c->hist, !c->plain);
+}
+
+// one FP32-phase iteration after Delta: FFT(z,t)+scale+IFFT(t,z), IFFT(x,y)+g, then
+// either (fused) the update fused with Delta, theta and F, links src -> dst, on
+// refresh iterations the FP32 links rebuilt from the input and Delta taken again,
+// and FFT(x,y); or the update in place writing the links' packed anti-Hermitian
+// parts, the refresh, and Delta+FFT(x,y)
+void launch_body32(lgf_ctx* c, cudaStream_t s, const float2* src, float2* dst)
+{
+    float2* Fd = reinterpret_cast<float2*>(c->Fd);
+    const Lat& d = c->lat32;
+    if (c->plain) {
+        launch_build_g<float>(d, s, Fd, c->g32, c->ctl);
+    } else {
+        launch_zt<float>(d, c->sh32, c->tb, s, Fd, c->ctl);
+        launch_xyinv_g<float>(d, c->sh32, c->tb, s, Fd, c->g32, c->ctl);
+    }
+    if (c->fused32) {
+        launch_update_delta32(d, s, src, dst, c->G32, c->g32, c->ctl, Fd, c->partials, c->hist);
+        if (c->refresh_every > 0) {
+            launch_refresh32(s, d, c->lat.ne, c->U64, c->G32, dst, nullptr, nullptr, c->ctl, c->refresh_every);
+            launch_delta_links32(d, s, dst, Fd, c->partials, c->ctl, c->hist, c->refresh_every);
+        }
+        if (!c->plain) launch_xy_fft<float>(d, c->sh32, c->tb, s, Fd, false);
+    } else {
+        launch_update<float>(d, s, c->U32, c->G32, c->g32, c->ctl, c->AH32, c->Fs32);
+        if (c->refresh_every > 0)
+            launch_refresh32(s, d, c->lat.ne, c->U64, c->G32, c->U32, c->AH32, c->Fs32, c->ctl, c->refresh_every);
+        launch_delta<float>(d, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, c->ctl, c->hist, !c->plain);
+    }
+}
+
+// Delta, theta and F of the FP32 phase's first links (U32), transformed along x,y
+void launch_start32(lgf_ctx* c, cudaStream_t s, Ctl* ctl, double2* hist)
+{
+    float2* Fd = reinterpret_cast<float2*>(c->Fd);
+    if (c->fused32) {
+        launch_delta_links32(c->lat32, s, c->U32, Fd, c->partials, ctl, hist, 0);
+        if (!c->plain) launch_xy_fft<float>(c->lat32, c->sh32, c->tb, s, Fd, false);
+    } else {
+        launch_ah_init<float>(c->lat32, s, c->U32, c->AH32, c->Fs32);
+        launch_delta<float>(c->lat32, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, ctl, hist, !c->plain);
+    }
 }
 
 // ---------------------------------------------------------------- graph
@@ -221,15 +257,33 @@ int add_while(cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, cudaGraph_t
     return LGF_OK;
 }
 
-template <typename T>
-int add_loop(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, vec2_t<T>* U, vec2_t<T>* G,
-             vec2_t<T>* g)
+// FP64 loop: one iteration per body run
+int add_loop64(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, double2* G)
 {
     cudaGraph_t body;
     cudaGraphConditionalHandle h;
     CKR(add_while(graph, deps, &body, &h));
     CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    launch_body<T>(c, c->cap, U, G, g);
+    launch_body64(c, c->cap, G);
+    launch_loop_ctl(c->cap, c->ctl, h);
+    CK(cudaGetLastError());
+    cudaGraph_t out;
+    CK(cudaStreamEndCapture(c->cap, &out));
+    return LGF_OK;
+}
+
+// FP32 loop: two iterations per body run, links U32 -> U32b -> U32 when the update
+// is fused with Delta, so that the two link buffers keep fixed roles in the graph
+// (when the first iteration ends the phase, every kernel of the second returns at
+// once); in place in U32 otherwise
+int add_loop32(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps)
+{
+    cudaGraph_t body;
+    cudaGraphConditionalHandle h;
+    CKR(add_while(graph, deps, &body, &h));
+    CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_body32(c, c->cap, c->U32, c->fused32 ? c->U32b : c->U32);
+    launch_body32(c, c->cap, c->fused32 ? c->U32b : c->U32, c->U32);
     launch_loop_ctl(c->cap, c->ctl, h);
     CK(cudaGetLastError());
     cudaGraph_t out;
@@ -245,25 +299,23 @@ int append_fix(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps
     if (c->mixed) {
         CKR(capture_begin(c, graph, deps));
         launch_mixed_prep(c->cap, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl);
-        launch_ah_init<float>(c->lat32, c->cap, c->U32, c->AH32, c->Fs32);
-        launch_delta<float>(c->lat32, c->sh32, c->tb, c->cap, c->AH32, c->Fs32, reinterpret_cast<float2*>(c->Fd),
-                            c->partials, c->ctl, c->hist, !c->plain);
+        launch_start32(c, c->cap, c->ctl, c->hist);
         CKR(capture_end(c, deps));
-        CKR(add_loop<float>(c, graph, deps, c->U32, c->G32, c->g32));
+        CKR(add_loop32(c, graph, deps));
         CKR(capture_begin(c, graph, deps));
         launch_switch(c->cap, c->lat, c->G32, c->g64, c->U64, c->G64, c->ctl);
         launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
         launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
                              !c->plain);
         CKR(capture_end(c, deps));
-        CKR(add_loop<double>(c, graph, deps, c->U64, c->G64, c->g64));
+        CKR(add_loop64(c, graph, deps, c->G64));
     } else {
         CKR(capture_begin(c, graph, deps));
         launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
         launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
                              !c->plain);
         CKR(capture_end(c, deps));
-        CKR(add_loop<double>(c, graph, deps, c->U64, c->track ? c->G64 : nullptr, c->g64));
+        CKR(add_loop64(c, graph, deps, c->track ? c->G64 : nullptr));
     }
     return LGF_OK;
 }
@@ -409,13 +461,17 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     CKR(alloc((void**)&c->AH64, 16 * Vs * sizeof(double2)));
     CKR(alloc((void**)&c->Fs64, Vs * sizeof(double)));
     if (c->mixed) {
+        CKR(alloc((void**)&c->U32, 24 * Vs * sizeof(float2)));
+        CKR(alloc((void**)&c->U32b, 24 * Vs * sizeof(float2)));
         CKR(alloc((void**)&c->AH32, 16 * Vs * sizeof(float2)));
         CKR(alloc((void**)&c->Fs32, Vs * sizeof(float)));
-        CKR(alloc((void**)&c->U32, 24 * Vs * sizeof(float2)));
         CKR(alloc((void**)&c->G32, 6 * Vs * sizeof(float2)));
         CKR(alloc((void**)&c->g32, 9 * Vs * sizeof(float2)));
     }
-    CKR(alloc((void**)&c->partials, 2 * (size_t)d.nplanes * sizeof(double)));
+    // block partial sums of theta and F: one pair per plane (Delta kernel) or per
+    // block of the site-parallel kernels, whichever grid is larger
+    const size_t nblk = (size_t)std::max(d.nplanes, update_grid(c->V));
+    CKR(alloc((void**)&c->partials, 2 * nblk * sizeof(double)));
     CKR(alloc((void**)&c->ctl, sizeof(Ctl)));
     CKR(alloc((void**)&c->ctl_stage, sizeof(Ctl)));
     CKR(alloc((void**)&c->hist, kHistCap * sizeof(double2)));
@@ -431,7 +487,7 @@ void free_all(lgf_ctx* c)
 {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
-                    c->hist, c->err, c->stage, c->tables, c->mult, c->AH64, c->Fs64, c->AH32, c->Fs32, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
+                    c->hist, c->err, c->stage, c->tables, c->mult, c->AH64, c->Fs64, c->U32b, c->AH32, c->Fs32, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
                     c->gl_part, c->gl_At, c->gl_D, c->wil_part, c->gen32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -536,8 +592,16 @@ template <typename T> int time_shape(lgf_ctx* c, const Shape& sh, int which, flo
     for (int r = 0; r <= reps; r++) {
         if (r == 1) cudaEventRecord(e0, s);
         if (which == 0) {
-            launch_delta<T>(lat_of<T>(c), sh, c->tb, s, ah_of<T>(c), fs_of<T>(c), Fd, c->partials, c->ctl_stage,
-                            nullptr, true);
+            // the plane kernels of the precision's iteration: FP64 Delta + FFT(x,y) and
+            // IFFT(x,y) + g; FP32 FFT(x,y) and IFFT(x,y) + g
+            if constexpr (sizeof(T) == 8)
+                launch_delta<double>(c->lat, sh, c->tb, s, c->AH64, c->Fs64, reinterpret_cast<double2*>(c->Fd),
+                                     c->partials, c->ctl_stage, nullptr, true);
+            else if (c->fused32)
+                launch_xy_fft<float>(c->lat32, sh, c->tb, s, reinterpret_cast<float2*>(c->Fd), false);
+            else
+                launch_delta<float>(c->lat32, sh, c->tb, s, c->AH32, c->Fs32, reinterpret_cast<float2*>(c->Fd),
+                                    c->partials, c->ctl_stage, nullptr, true);
             launch_xyinv_g<T>(lat_of<T>(c), sh, c->tb, s, Fd, g_of<T>(c), c->ctl_stage);
         } else {
             launch_zt<T>(lat_of<T>(c), sh, c->tb, s, Fd, c->ctl_stage);
@@ -609,7 +673,7 @@ int autotune_ctx(lgf_ctx* c)
     CKR(autotune_prec<double>(c));
     if (c->mixed) {
         launch_mixed_prep(c->stream, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl_stage);
-        launch_ah_init<float>(c->lat32, c->stream, c->U32, c->AH32, c->Fs32);
+        launch_start32(c, c->stream, c->ctl_stage, nullptr);
         CKR(autotune_prec<float>(c));
     }
     CK(cudaStreamSynchronize(c->stream));
@@ -807,6 +871,16 @@ int lgf_set_fp32_refresh(lgf_ctx* c, int every)
     if (every != c->refresh_every) {
         c->refresh_every = every;
         drop_graph(c);  // the interval is a launch argument of the captured body
+    }
+    return LGF_OK;
+}
+
+int lgf_set_fp32_update(lgf_ctx* c, int fused)
+{
+    if (!c || (fused != 0 && fused != 1)) return LGF_ERR_ARG;
+    if (c->fused32 != (fused == 1)) {
+        c->fused32 = fused == 1;
+        drop_graph(c);
     }
     return LGF_OK;
 }
@@ -1015,7 +1089,7 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
     int rc = LGF_OK;
     if (precision == 32) {
         launch_mixed_prep(s, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl_stage);
-        launch_ah_init<float>(c->lat32, s, c->U32, c->AH32, c->Fs32);
+        launch_start32(c, s, c->ctl_stage, nullptr);
     } else {
         launch_ah_init<double>(c->lat, s, c->U64, c->AH64, c->Fs64);
     }
@@ -1033,15 +1107,25 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
             launch_update<double>(c->lat, s, c->U64, c->track ? c->G64 : nullptr, c->g64, c->ctl_stage, c->AH64,
                                   c->Fs64);
         } else {
+            // FP32 phase.  Fused: FFT(x,y) alone, then z,t, IFFT(x,y) + g, and the update
+            // fused with Delta, theta and F (links alternate between the two buffers).
+            // Otherwise: Delta + FFT(x,y), z,t, IFFT(x,y) + g, the update.
             float2* Fd = reinterpret_cast<float2*>(c->Fd);
-            launch_delta<float>(c->lat32, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, c->ctl_stage, nullptr,
-                                true);
+            if (c->fused32)
+                launch_xy_fft<float>(c->lat32, c->sh32, c->tb, s, Fd, false);
+            else
+                launch_delta<float>(c->lat32, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, c->ctl_stage,
+                                    nullptr, true);
             cudaEventRecord(ev[1], s);
             launch_zt<float>(c->lat32, c->sh32, c->tb, s, Fd, c->ctl_stage);
             cudaEventRecord(ev[2], s);
             launch_xyinv_g<float>(c->lat32, c->sh32, c->tb, s, Fd, c->g32, c->ctl_stage);
             cudaEventRecord(ev[3], s);
-            launch_update<float>(c->lat32, s, c->U32, c->G32, c->g32, c->ctl_stage, c->AH32, c->Fs32);
+            if (c->fused32)
+                launch_update_delta32(c->lat32, s, (it & 1) ? c->U32b : c->U32, (it & 1) ? c->U32 : c->U32b,
+                                      c->G32, c->g32, c->ctl_stage, Fd, c->partials, nullptr);
+            else
+                launch_update<float>(c->lat32, s, c->U32, c->G32, c->g32, c->ctl_stage, c->AH32, c->Fs32);
         }
         cudaEventRecord(ev[4], s);
         cudaError_t e = cudaEventSynchronize(ev[4]);

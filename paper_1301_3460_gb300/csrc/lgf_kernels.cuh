@@ -55,6 +55,27 @@ __host__ __device__ inline size_t pencil_smem_bytes(const Lat& d, int xw, size_t
     return (size_t)d.L[3] * pencil_rs(d, xw, elem) * elem + (size_t)xw * d.L[2] * d.L[3] * (elem / 2);
 }
 
+// dst[i] = src(i) for i < n over the block, K loads in flight per thread before
+// their stores (a load-then-store loop would wait out one memory latency per value)
+template <int K, typename V, typename SRC, typename DST>
+__device__ __forceinline__ void block_copy(int n, SRC src, DST dst)
+{
+    const int nt = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < n; i0 += K * nt) {
+        V v[K];
+#pragma unroll
+        for (int u = 0; u < K; u++) {
+            const int i = i0 + u * nt;
+            if (i < n) v[u] = src(i);
+        }
+#pragma unroll
+        for (int u = 0; u < K; u++) {
+            const int i = i0 + u * nt;
+            if (i < n) dst(i, v[u]);
+        }
+    }
+}
+
 // Transform nlines lines of length L (forward, or inverse when INV): each line
 // is read through ld(line, position) and written through st(line, position,
 // value), positions 0..L-1 along the line in natural order (time in, frequency
@@ -62,7 +83,7 @@ __host__ __device__ inline size_t pencil_smem_bytes(const Lat& d, int xw, size_t
 // line (line_lanes(L) of them) work together, so every thread of the block
 // calls this with the same nlines; lines are dealt out a warp at a time.
 template <typename T, int L, bool INV, typename LD, typename ST>
-__device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st, const vec2_t<T>* __restrict__ tw)
+__device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st)
 {
     constexpr int Tl = line_lanes<T>(L), R = L / Tl, W = 32 / Tl;
     const int lane = (int)threadIdx.x & 31, tau = lane / W, w = lane - tau * W;
@@ -74,8 +95,8 @@ __device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st, const vec2_
         cx<T> v[R];
 #pragma unroll
         for (int j = 0; j < R; j++) v[j] = ld(lc, INV ? line_pos_k<T, L>(tau, j) : line_pos_x<T, L>(tau, j));
-        if constexpr (INV) line_inv<T, L>(v, tau, tw);
-        else line_fwd<T, L>(v, tau, tw);
+        if constexpr (INV) line_inv<T, L>(v, tau);
+        else line_fwd<T, L>(v, tau);
         if (ok) {
 #pragma unroll
             for (int j = 0; j < R; j++) st(l, INV ? line_pos_x<T, L>(tau, j) : line_pos_k<T, L>(tau, j), v[j]);
@@ -86,7 +107,7 @@ __device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st, const vec2_
 // Forward transform, a real multiplier per frequency m(line, k), inverse
 // transform, in one pass over the lines (natural order in and out).
 template <typename T, int L, typename LD, typename MUL, typename ST>
-__device__ __forceinline__ void lines_accel(int nlines, LD ld, MUL mul, ST st, const vec2_t<T>* __restrict__ tw)
+__device__ __forceinline__ void lines_accel(int nlines, LD ld, MUL mul, ST st)
 {
     constexpr int Tl = line_lanes<T>(L), R = L / Tl, W = 32 / Tl;
     const int lane = (int)threadIdx.x & 31, tau = lane / W, w = lane - tau * W;
@@ -98,14 +119,14 @@ __device__ __forceinline__ void lines_accel(int nlines, LD ld, MUL mul, ST st, c
         cx<T> v[R];
 #pragma unroll
         for (int j = 0; j < R; j++) v[j] = ld(lc, line_pos_x<T, L>(tau, j));
-        line_fwd<T, L>(v, tau, tw);
+        line_fwd<T, L>(v, tau);
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const T m = mul(lc, line_pos_k<T, L>(tau, r));
             v[r].re *= m;
             v[r].im *= m;
         }
-        line_inv<T, L>(v, tau, tw);
+        line_inv<T, L>(v, tau);
         if (ok) {
 #pragma unroll
             for (int j = 0; j < R; j++) st(l, line_pos_x<T, L>(tau, j), v[j]);
@@ -115,7 +136,7 @@ __device__ __forceinline__ void lines_accel(int nlines, LD ld, MUL mul, ST st, c
 
 // The x-lines (rows) of the four fields of a plane tile, in place.
 template <typename T, bool INV>
-__device__ __forceinline__ void tile_x_lines(const Lat& d, vec2_t<T>* sm, const vec2_t<T>* __restrict__ tw)
+__device__ __forceinline__ void tile_x_lines(const Lat& d, vec2_t<T>* sm)
 {
     const int Ly = d.L[1], rsx = plane_rsx(d), fs = plane_fs(d);
     with_length(d.L[0], [&](auto Lc) {
@@ -126,7 +147,7 @@ __device__ __forceinline__ void tile_x_lines(const Lat& d, vec2_t<T>* sm, const 
         };
         lines_pass<T, L, INV>(
             4 * Ly, [&](int l, int e) { return ldv<T>(row(l) + e); },
-            [&](int l, int e, cx<T> v) { st<T>(row(l) + e, v); }, tw);
+            [&](int l, int e, cx<T> v) { st<T>(row(l) + e, v); });
     });
 }
 
@@ -135,8 +156,7 @@ __device__ __forceinline__ void tile_x_lines(const Lat& d, vec2_t<T>* sm, const 
 // src_fs and row stride src_rs), transformed, stored to dst likewise.
 template <typename T, bool INV>
 __device__ __forceinline__ void plane_y_lines(const Lat& d, const vec2_t<T>* src, int src_fs, int src_rs,
-                                              vec2_t<T>* dst, int dst_fs, int dst_rs,
-                                              const vec2_t<T>* __restrict__ tw)
+                                              vec2_t<T>* dst, int dst_fs, int dst_rs)
 {
     // offsets stay 32-bit: four fields of V sites, V < 2^31 / 24
     const int Lx = d.L[0];
@@ -151,8 +171,7 @@ __device__ __forceinline__ void plane_y_lines(const Lat& d, const vec2_t<T>* src
             [&](int l, int e, cx<T> v) {
                 const int f = l / Lx, x = l - f * Lx;
                 st<T>(dst + (f * dst_fs + e * dst_rs + x), v);
-            },
-            tw);
+            });
     });
 }
 
@@ -309,6 +328,13 @@ template <typename T> __device__ __forceinline__ void ah_pack(const cx<T>* w, cx
     a[3] = mk<T>((T)2 * (w[0].im - t), (T)2 * (w[4].im - t));
 }
 
+// per-site sum of |Delta_ij|^2 of the packed Delta, in T
+template <typename T> __device__ __forceinline__ T theta_site(const cx<T>* D)
+{
+    const T p = D[3].re, q = D[3].im, pq = p + q;
+    return (T)2 * (norm2(D[0]) + norm2(D[1]) + norm2(D[2])) + p * p + q * q + pq * pq;
+}
+
 // ah of every link and the per-site sum of Re Tr over the four links, from
 // links whose row 2 is rebuilt (before the first iteration; the update kernel
 // writes them for the links it produces).  AH: [mu=4][k=4][V], Fs: [V].
@@ -339,8 +365,7 @@ __global__ void __launch_bounds__(256) k_ah_init(Lat d, const vec2_t<T>* __restr
 template <typename T, bool FFT>
 __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const vec2_t<T>* __restrict__ AH, const T* __restrict__ Fs,
                                                vec2_t<T>* __restrict__ Fd, double* __restrict__ partials, Ctl* ctl,
-                                               double2* hist, const vec2_t<T>* __restrict__ twx,
-                                               const vec2_t<T>* __restrict__ twy)
+                                               double2* hist)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
@@ -376,10 +401,9 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const v
 #pragma unroll
             for (int mu = 1; mu < 4; mu++) D[k] = D[k] + a[4 * mu + k] - b[4 * mu + k];
         }
-        const T p = D[3].re, q = D[3].im, pq = p + q;
         // per-site sum of |Delta_ij|^2 in the kernel's precision, accumulated over
         // sites in FP64
-        th += (double)((T)2 * (norm2(D[0]) + norm2(D[1]) + norm2(D[2])) + p * p + q * q + pq * pq);
+        th += (double)theta_site(D);
         if (FFT) {
 #pragma unroll
             for (int k = 0; k < 4; k++) st<T>(sm + k * fs + y * rsx + x, D[k]);
@@ -391,9 +415,9 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const v
     reduce_theta_F(th, fsum, partials, ctl, hist, V);
     if (FFT) {
         __syncthreads();
-        tile_x_lines<T, false>(d, sm, twx);
+        tile_x_lines<T, false>(d, sm);
         __syncthreads();
-        plane_y_lines<T, false>(d, sm, fs, rsx, Fd + s0, V, Lx, twy);
+        plane_y_lines<T, false>(d, sm, fs, rsx, Fd + s0, V, Lx);
     }
 }
 
@@ -409,7 +433,6 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const v
 // written to Fd.
 template <typename T>
 __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_zt(Lat d, int xw, vec2_t<T>* __restrict__ Fd, const Ctl* ctl,
-                                            const vec2_t<T>* __restrict__ twz, const vec2_t<T>* __restrict__ twt,
                                             const T* __restrict__ mult)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -422,12 +445,17 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_zt(Lat d, int xw, ve
     vec2_t<T>* g = Fd + (size_t)blockIdx.z * d.V + c0;
     T* msm = reinterpret_cast<T*>(sm + Lt * rs);
     {
-        const int n = xw * Lz * Lt;
+        // FP32: the step's alpha/2 is folded in here, so that the FP64 g builder
+        // (k_xyinv_g<float, float>) receives alpha/2 Delta~ and saves its multiplies
+        const T hs = sizeof(T) == 4 ? (T)(0.5 * ctl->alpha) : (T)1;
         const T* mrow = mult + c0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int zt = i / xw, xi = i - zt * xw;
-            msm[i] = __ldg(mrow + (xi + P * zt));
-        }
+        block_copy<8, T>(
+            xw * Lz * Lt,
+            [&](int i) {
+                const int zt = i / xw, xi = i - zt * xw;
+                return __ldg(mrow + (xi + P * zt));
+            },
+            [&](int i, T v) { msm[i] = v * hs; });
     }
     // z forward: lines (xi, t)
     with_length(Lz, [&](auto Lc) {
@@ -441,8 +469,7 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_zt(Lat d, int xw, ve
             [&](int l, int e, cx<T> v) {
                 const int tt = l / xw, xi = l - tt * xw;
                 st<T>(sm + tt * rs + e * xw + xi, v);
-            },
-            twz);
+            });
     });
     __syncthreads();
     // t forward, accelerator, t inverse: lines (xi, kz)
@@ -451,7 +478,7 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_zt(Lat d, int xw, ve
         lines_accel<T, L>(
             xw * Lz, [&](int l, int e) { return ldv<T>(sm + e * rs + l); },
             [&](int l, int k) { return msm[l + xw * Lz * k]; },
-            [&](int l, int e, cx<T> v) { st<T>(sm + e * rs + l, v); }, twt);
+            [&](int l, int e, cx<T> v) { st<T>(sm + e * rs + l, v); });
     });
     __syncthreads();
     // z inverse: lines (xi, t), back to Fd
@@ -466,8 +493,7 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_zt(Lat d, int xw, ve
             [&](int l, int e, cx<T> v) {
                 const int tt = l / xw, xi = l - tt * xw;
                 st<T>(g + (xi + P * (e + L * tt)), v);
-            },
-            twz);
+            });
     });
 }
 
@@ -537,9 +563,7 @@ __device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>
 // Gram-Schmidt in FP64 whatever T is; g stored as TG.
 template <typename T, typename TG>
 __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
-                                                 vec2_t<TG>* __restrict__ g, const Ctl* ctl,
-                                                 const vec2_t<T>* __restrict__ twx,
-                                                 const vec2_t<T>* __restrict__ twy)
+                                                 vec2_t<TG>* __restrict__ g, const Ctl* ctl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
@@ -547,23 +571,33 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xyinv_g(Lat d, const
     const int P = d.P, V = d.V, Lx = d.L[0];
     const int s0 = blockIdx.x * P;
     const int rsx = plane_rsx(d), fs = plane_fs(d);
-    plane_y_lines<T, true>(d, Fd + s0, V, Lx, sm, fs, rsx, twy);
+    plane_y_lines<T, true>(d, Fd + s0, V, Lx, sm, fs, rsx);
     __syncthreads();
-    tile_x_lines<T, true>(d, sm, twx);
+    tile_x_lines<T, true>(d, sm);
     __syncthreads();
-    const double h = 0.5 * ctl->alpha;
     for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
         const int y = xy / Lx, x = xy - y * Lx;
         const int o = y * rsx + x;
         vec2_t<T> f0 = sm[o], f1 = sm[fs + o], f2 = sm[2 * fs + o], f3 = sm[3 * fs + o];
-        // X = 1 + (alpha/2) Delta~ ; rows 0 and 1
+        // X = 1 + (alpha/2) Delta~ ; rows 0 and 1 (FP32 fields arrive already
+        // multiplied by alpha/2, in the z,t kernel)
         cx<double> X[6];
-        X[0] = mk<double>(1.0, h * (double)f3.x);
-        X[1] = mk<double>(h * (double)f0.x, h * (double)f0.y);
-        X[2] = mk<double>(h * (double)f1.x, h * (double)f1.y);
-        X[3] = mk<double>(-h * (double)f0.x, h * (double)f0.y);  // -conj(Delta01)
-        X[4] = mk<double>(1.0, h * (double)f3.y);
-        X[5] = mk<double>(h * (double)f2.x, h * (double)f2.y);
+        if constexpr (sizeof(T) == 4) {
+            X[0] = mk<double>(1.0, (double)f3.x);
+            X[1] = mk<double>((double)f0.x, (double)f0.y);
+            X[2] = mk<double>((double)f1.x, (double)f1.y);
+            X[3] = mk<double>(-(double)f0.x, (double)f0.y);  // -conj(Delta01)
+            X[4] = mk<double>(1.0, (double)f3.y);
+            X[5] = mk<double>((double)f2.x, (double)f2.y);
+        } else {
+            const double h = 0.5 * ctl->alpha;
+            X[0] = mk<double>(1.0, h * f3.x);
+            X[1] = mk<double>(h * f0.x, h * f0.y);
+            X[2] = mk<double>(h * f1.x, h * f1.y);
+            X[3] = mk<double>(-h * f0.x, h * f0.y);  // -conj(Delta01)
+            X[4] = mk<double>(1.0, h * f3.y);
+            X[5] = mk<double>(h * f2.x, h * f2.y);
+        }
         // Gram-Schmidt in FP64; row 2 = conj(r0 x r1) in the precision g is
         // stored in (for an FP32 g, from the rounded rows, so that the stored g
         // is unitary to FP32 rounding)
@@ -609,6 +643,53 @@ __global__ void __launch_bounds__(256) k_build_g(Lat d, const vec2_t<T>* __restr
 
 // ---------------------------------------------------------------- k_update
 
+// w = ga u gb^dag for full 3x3 ga, u, gb: rows 0,1 as two 2x3-by-3x3 products,
+// row 2 rebuilt as conj(row0 x row1) (the 12-real form of the result)
+template <typename T>
+__device__ __forceinline__ void link_gug(const cx<T>* ga, const cx<T>* u, const cx<T>* gb, cx<T>* w)
+{
+    cx<T> A[6];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cx<T> acc = cmul(ga[3 * i], u[j]);
+            acc = cmac(acc, ga[3 * i + 1], u[3 + j]);
+            acc = cmac(acc, ga[3 * i + 2], u[6 + j]);
+            A[3 * i + j] = acc;
+        }
+    // w_ij = sum_k A_ik conj(gb_jk)
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cx<T> acc = cmulc(A[3 * i], gb[3 * j]);
+            acc = cmacc(acc, A[3 * i + 1], gb[3 * j + 1]);
+            acc = cmacc(acc, A[3 * i + 2], gb[3 * j + 2]);
+            w[3 * i + j] = acc;
+        }
+    complete_row2(w, w + 6);
+}
+
+// G(x) <- g(x) G(x), rows 0,1 stored (row 2 of G rebuilt on load)
+template <typename T>
+__device__ __forceinline__ void gauge_accumulate(vec2_t<T>* __restrict__ G, int V, int s, const cx<T>* gx)
+{
+    cx<T> Gm[9];
+#pragma unroll
+    for (int e = 0; e < 6; e++) Gm[e] = ldv<T>(G + (size_t)e * V + s);
+    complete_row2(Gm, Gm + 6);
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cx<T> acc = cmul(gx[3 * i], Gm[j]);
+            acc = cmac(acc, gx[3 * i + 1], Gm[3 + j]);
+            acc = cmac(acc, gx[3 * i + 2], Gm[6 + j]);
+            st<T>(G + (size_t)(3 * i + j) * V + s, acc);
+        }
+}
+
 // One thread per site.  G may be null (gauge not tracked).  Also writes the
 // packed anti-Hermitian parts of the new links (AH) and their Re Tr per site
 // (Fs) for the next Delta.
@@ -634,33 +715,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
     T f = 0;
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
-        cx<T> u[9];
+        cx<T> u[9], gn[9], w[9];
         load_link<T>(U, V, d.ne, mu, s, u);
-        // A = rows 0,1 of g(x) U
-        cx<T> A[6];
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                cx<T> acc = cmul(gx[3 * i], u[j]);
-                acc = cmac(acc, gx[3 * i + 1], u[3 + j]);
-                acc = cmac(acc, gx[3 * i + 2], u[6 + j]);
-                A[3 * i + j] = acc;
-            }
-        cx<T> gn[9];
         load_g<T>(g, V, site_shift(d, s, c[mu], mu, +1), gn);
-        // U' = A g^dag(x+mu): U'_ij = sum_k A_ik conj(gn_jk); row 2 rebuilt
-        cx<T> w[9];
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                cx<T> acc = cmulc(A[3 * i], gn[3 * j]);
-                acc = cmacc(acc, A[3 * i + 1], gn[3 * j + 1]);
-                acc = cmacc(acc, A[3 * i + 2], gn[3 * j + 2]);
-                w[3 * i + j] = acc;
-            }
-        complete_row2(w, w + 6);
+        link_gug(gx, u, gn, w);
         store_link<T>(U, V, d.ne, mu, s, w);
         cx<T> a[4];
         ah_pack(w, a);
@@ -669,21 +727,113 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
         f += w[0].re + w[4].re + w[8].re;
     }
     Fs[s] = f;
-    if (G != nullptr) {
-        cx<T> Gm[9];
-#pragma unroll
-        for (int e = 0; e < 6; e++) Gm[e] = ldv<T>(G + (size_t)e * V + s);
-        complete_row2(Gm, Gm + 6);
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                cx<T> acc = cmul(gx[3 * i], Gm[j]);
-                acc = cmac(acc, gx[3 * i + 1], Gm[3 + j]);
-                acc = cmac(acc, gx[3 * i + 2], Gm[6 + j]);
-                st<T>(G + (size_t)(3 * i + j) * V + s, acc);
-            }
+    if (G != nullptr) gauge_accumulate<T>(G, V, s, gx);
+}
+
+// ---------------------------------------------------------------- fused update and Delta
+
+// The update fused with the Delta stencil (the form of the FP32 phase, where
+// recomputing a neighbour's link costs less than moving its anti-Hermitian part
+// through memory).  One thread per site x:
+//   U'_mu(x) = g(x) U_mu(x) g^dag(x+mu), stored to Uout, and G(x) <- g(x) G(x);
+//   the links entering x, U'_mu(x-mu) = g(x-mu) U_mu(x-mu) g^dag(x), recomputed
+//   from Uin for their anti-Hermitian parts only;
+//   Delta(x) = sum_mu ah(U'_mu(x-mu)) - ah(U'_mu(x)) stored to Fd (packed, in
+//   space), theta and F of the new links reduced in FP64, the loop state updated.
+// Uin and Uout are different buffers: a thread reads its neighbours' old links,
+// which their own threads replace in the same launch.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_update_delta(
+    Lat d, const vec2_t<T>* __restrict__ Uin, vec2_t<T>* __restrict__ Uout, vec2_t<T>* __restrict__ G,
+    const vec2_t<T>* __restrict__ g, Ctl* ctl, vec2_t<T>* __restrict__ Fd, double* __restrict__ partials,
+    double2* hist)
+{
+    if (ld_flag(&ctl->phase_done)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->iter += 1;
+        if (ctl->phase == 0) ctl->iter_phase0 += 1;
     }
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double th = 0.0, fsum = 0.0;
+    if (s < V) {
+        int c[4];
+        site_coords(d, s, c);
+        cx<T> gx[9];
+        load_g<T>(g, V, s, gx);
+        cx<T> D[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) D[k] = mk<T>(0, 0);
+        T f = 0;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            cx<T> u[9], gn[9], w[9], a[4];
+            // the link leaving x
+            load_link<T>(Uin, V, d.ne, mu, s, u);
+            load_g<T>(g, V, site_shift(d, s, c[mu], mu, +1), gn);
+            link_gug(gx, u, gn, w);
+            store_link<T>(Uout, V, d.ne, mu, s, w);
+            ah_pack(w, a);
+#pragma unroll
+            for (int k = 0; k < 4; k++) D[k] = D[k] - a[k];
+            f += w[0].re + w[4].re + w[8].re;
+            // the link entering x from x - mu
+            const int sb = site_shift(d, s, c[mu], mu, -1);
+            load_link<T>(Uin, V, d.ne, mu, sb, u);
+            load_g<T>(g, V, sb, gn);
+            link_gug(gn, u, gx, w);
+            ah_pack(w, a);
+#pragma unroll
+            for (int k = 0; k < 4; k++) D[k] = D[k] + a[k];
+        }
+        if (G != nullptr) gauge_accumulate<T>(G, V, s, gx);
+#pragma unroll
+        for (int k = 0; k < 4; k++) st<T>(Fd + (size_t)k * V + s, D[k]);
+        th = (double)theta_site(D);
+        fsum = (double)f;
+    }
+    reduce_theta_F(th, fsum, partials, ctl, hist, V);
+}
+
+// Delta, theta and F of the stored links themselves (no update): the start of
+// the FP32 phase and, when `every` > 0, the iterations on which the FP32 links
+// were rebuilt from the FP64 input (the refresh).  Delta in space to Fd.
+template <typename T>
+__global__ void __launch_bounds__(256) k_delta_links(Lat d, const vec2_t<T>* __restrict__ U,
+                                                     vec2_t<T>* __restrict__ Fd, double* __restrict__ partials,
+                                                     Ctl* ctl, double2* hist, int every)
+{
+    if (ld_flag(&ctl->phase_done)) return;
+    if (every > 0 && !(ctl->phase == 0 && ctl->iter > 0 && ctl->iter % every == 0)) return;
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double th = 0.0, fsum = 0.0;
+    if (s < V) {
+        int c[4];
+        site_coords(d, s, c);
+        cx<T> D[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) D[k] = mk<T>(0, 0);
+        T f = 0;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            cx<T> u[9], a[4];
+            load_link<T>(U, V, d.ne, mu, s, u);
+            ah_pack(u, a);
+#pragma unroll
+            for (int k = 0; k < 4; k++) D[k] = D[k] - a[k];
+            f += u[0].re + u[4].re + u[8].re;
+            load_link<T>(U, V, d.ne, mu, site_shift(d, s, c[mu], mu, -1), u);
+            ah_pack(u, a);
+#pragma unroll
+            for (int k = 0; k < 4; k++) D[k] = D[k] + a[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) st<T>(Fd + (size_t)k * V + s, D[k]);
+        th = (double)theta_site(D);
+        fsum = (double)f;
+    }
+    reduce_theta_F(th, fsum, partials, ctl, hist, V);
 }
 
 // ---------------------------------------------------------------- loop control

@@ -48,6 +48,14 @@ void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t
 template <typename T>
 void launch_update(const Lat& d, cudaStream_t s, vec2_t<T>* U, vec2_t<T>* G, const vec2_t<T>* g, Ctl* ctl,
                    vec2_t<T>* AH, T* Fs);
+// FP32 phase: the update fused with Delta, theta and F (links Uin -> Uout, Delta
+// in space to Fd), and Delta, theta and F of stored links (every > 0: only on
+// the FP32 phase's refresh iterations); grids of update_grid(V) blocks
+int update_grid(int V);
+void launch_update_delta32(const Lat& d, cudaStream_t s, const float2* Uin, float2* Uout, float2* G, const float2* g,
+                           Ctl* ctl, float2* Fd, double* partials, double2* hist);
+void launch_delta_links32(const Lat& d, cudaStream_t s, const float2* U, float2* Fd, double* partials, Ctl* ctl,
+                          double2* hist, int every);
 
 // conversion, checking and mode-switch kernels (FP64 unit)
 void launch_pack_links64(cudaStream_t s, int V, int ne, const double* in, double2* U, unsigned long long* err);

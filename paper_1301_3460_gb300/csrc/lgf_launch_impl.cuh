@@ -12,9 +12,6 @@ template <typename T> inline const T* mult_of(const Tables& tb);
 template <> inline const double* mult_of<double>(const Tables& tb) { return tb.mult64; }
 template <> inline const float* mult_of<float>(const Tables& tb) { return tb.mult32; }
 
-template <typename T> inline const vec2_t<T>* tw_of(const Tables& tb, int mu);
-template <> inline const double2* tw_of<double>(const Tables& tb, int mu) { return tb.tw64[mu]; }
-template <> inline const float2* tw_of<float>(const Tables& tb, int mu) { return tb.tw32[mu]; }
 
 template <typename T> inline size_t xy_smem(const Lat& d) { return plane_smem_bytes(d, sizeof(vec2_t<T>)); }
 template <typename T> inline size_t zt_smem(const Lat& d, const Shape& sh)
@@ -54,11 +51,9 @@ void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t 
                   vec2_t<T>* Fd, double* partials, Ctl* ctl, double2* hist, bool fft)
 {
     if (fft)
-        k_delta<T, true><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist,
-                                                                    tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+        k_delta<T, true><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
     else
-        k_delta<T, false><<<d.nplanes, sh.nt_xy, 0, s>>>(d, AH, Fs, Fd, partials, ctl, hist, tw_of<T>(tb, 0),
-                                                         tw_of<T>(tb, 1));
+        k_delta<T, false><<<d.nplanes, sh.nt_xy, 0, s>>>(d, AH, Fs, Fd, partials, ctl, hist);
 }
 
 template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const vec2_t<T>* U, vec2_t<T>* AH, T* Fs)
@@ -70,15 +65,14 @@ template <typename T>
 void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl)
 {
     const dim3 grid(d.L[0] / sh.xw, d.L[1], 4);
-    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tw_of<T>(tb, 2), tw_of<T>(tb, 3),
-                                                      mult_of<T>(tb));
+    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, mult_of<T>(tb));
 }
 
 template <typename T>
 void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* Fd,
                     vec2_t<T>* g, const Ctl* ctl)
 {
-    k_xyinv_g<T, T><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+    k_xyinv_g<T, T><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl);
 }
 
 template <typename T> void launch_build_g(const Lat& d, cudaStream_t s, const vec2_t<T>* Fd, vec2_t<T>* g, const Ctl* ctl)
@@ -91,9 +85,9 @@ void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t
 {
     const size_t sm = xy_smem<T>(d);
     if (inv)
-        k_xy_fft<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+        k_xy_fft<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
     else
-        k_xy_fft<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd, tw_of<T>(tb, 0), tw_of<T>(tb, 1));
+        k_xy_fft<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
 }
 
 template <typename T>

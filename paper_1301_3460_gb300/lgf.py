@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
             "lgf_get_stats": ([P, IP, IP], I),
             "lgf_set_switch_tol": ([P, D], I),
             "lgf_set_fp32_refresh": ([P, I], I),
+            "lgf_set_fp32_update": ([P, I], I),
             "lgf_set_loop_bound": ([P, I], I),
             "lgf_delta": ([P, P, I, DP, DP], I),
             "lgf_accelerate": ([P, P, P, I], I),
@@ -211,6 +212,10 @@ class Lattice:
 
     def set_fp32_refresh(self, every: int):
         _check(self._lib.lgf_set_fp32_refresh(self._h, int(every)), "lgf_set_fp32_refresh")
+
+    def set_fp32_update(self, fused: bool):
+        """FP32 phase: update fused with Delta (True) or the two-kernel form (False)."""
+        _check(self._lib.lgf_set_fp32_update(self._h, 1 if fused else 0), "lgf_set_fp32_update")
 
     def set_links(self, U):
         p, dev, keep = _in_ptr(U, (4, self.V, 3, 3))

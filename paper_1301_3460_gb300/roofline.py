@@ -21,7 +21,14 @@ FP64 path, per site (V sites per launch):
                 (2 x 132), row 2 of the result (42), packing (12), Re Tr (2);
                 G: rebuild (42) + one product (132).
 FP32 kernels move half the bytes of every array they keep in FP32 (links, G, g,
-fields, packed parts, multiplier); their flop counts are the same.
+fields, packed parts, multiplier); their flop counts are the same.  The FP32
+phase's default form fuses Delta into the update (fused=True):
+  delta_xyfft   the forward x,y FFT alone: reads and writes the 4 fields (32 + 32 B).
+  update        reads links, g, G; writes links, G and Delta: 192 + 72 + 48 + 192 +
+                48 + 32 B (the neighbours' links and g that it also reads are other
+                sites' data, counted once).  Flops: the four links leaving the site
+                as above, the four entering it recomputed for their anti-Hermitian
+                parts (4 x (42 + 2 x 132 + 42 + 12)), G, Delta (64), theta and F (21).
 
 Wilson-action generation (k_wilson, one launch per direction and checkerboard
 parity), per link updated, with full 3x3 complex products of 198 flops (27
@@ -43,11 +50,20 @@ import math
 KERNELS = ("delta_xyfft", "zt_fft_accel", "xyifft_g", "update")
 
 
-def per_site(dims, precision: int = 64) -> dict:
+def per_site(dims, precision: int = 64, fused32: bool = True) -> dict:
     Lx, Ly, Lz, Lt = (int(v) for v in dims)
     w = 1.0 if precision == 64 else 0.5
     lxy = math.log2(Lx * Ly)
     lzt = math.log2(Lz * Lt)
+    if precision == 32 and fused32:
+        return {
+            "delta_xyfft": dict(bytes=(64 + 64) * w, flops=4 * 5 * lxy),
+            "zt_fft_accel": dict(bytes=(8 + 64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
+            "xyifft_g": dict(bytes=(64 + 144) * w, flops=4 * 5 * lxy + 134),
+            "update": dict(bytes=(384 + 144 + 96 + 384 + 96 + 64) * w,
+                           flops=4 * (42 + 2 * 132 + 42 + 12 + 2) + 4 * (42 + 2 * 132 + 42 + 12) + 42 + 132
+                           + 64 + 21),
+        }
     return {
         "delta_xyfft": dict(bytes=(256 + 8 + 64) * w, flops=64 + 21 + 4 * 5 * lxy),
         "zt_fft_accel": dict(bytes=(8 + 64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
@@ -57,11 +73,11 @@ def per_site(dims, precision: int = 64) -> dict:
     }
 
 
-def per_iteration(dims, precision: int = 64) -> dict:
+def per_iteration(dims, precision: int = 64, fused32: bool = True) -> dict:
     V = 1
     for v in dims:
         V *= int(v)
-    ps = per_site(dims, precision)
+    ps = per_site(dims, precision, fused32)
     return dict(bytes=V * sum(k["bytes"] for k in ps.values()), flops=V * sum(k["flops"] for k in ps.values()))
 
 

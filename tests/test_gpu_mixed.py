@@ -58,19 +58,23 @@ def test_mixed_full_size_against_fp64_gpu():
     assert err < 1e-4
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("autotune", [False, True])
-@pytest.mark.parametrize("L,seed", [((8, 8, 8, 8), 1001), ((16, 16, 16, 16), 1601), ((8, 8, 32, 32), 3301)])
-def test_fp32_phase_follows_the_fp64_iteration(L, seed, autotune):
+@pytest.mark.parametrize("L,seed", [((8, 8, 8, 8), 1001), ((16, 16, 16, 16), 1601), ((8, 8, 32, 32), 3301),
+                                    ((12, 6, 24, 48), 3302)])
+def test_fp32_phase_follows_the_fp64_iteration(L, seed, autotune, fused):
     """The FP32 phase is the FP64 iteration to FP32 rounding: theta_n of its first
     eight updates matches the oracle's to 1e-5 relative (measured 5e-8 to 1.3e-7:
     a few FP32 roundings) and the links after them (re-projected in FP64) to 1e-4
     (measured 1.2e-6 to 2.3e-6), with the default launch shapes and with the
-    autotuned ones (at the default pencil width of 8 columns these extents,
-    Lz = Lt <= 32, take the register-line z,t transform).  A wrong mode anywhere in the FP32 Delta, transforms,
-    accelerator or update shows at O(1)."""
+    autotuned ones, with the update fused with Delta and in the two-kernel form,
+    on radix-2 and radix-3 extents (two lanes per line at 24, 32 and 48).  A
+    wrong mode anywhere in the FP32 Delta, transforms, accelerator or update
+    shows at O(1)."""
     U = inputs.rough_gauge_field(L, 0.3, seed)
     ref = orc.fix(L, U, alpha=0.08, tol=0.0, max_iter=8, history=True)
     with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_fp32_update(fused)
         lat.set_switch_tol(0.0)
         lat.set_links(U)
         if autotune:
@@ -86,6 +90,24 @@ def test_fp32_phase_follows_the_fp64_iteration(L, seed, autotune):
                                                                         np.abs(Um - ref["U"]).max()))
     assert rel.max() < 1e-5
     assert np.max(np.abs(Um - ref["U"])) < 1e-4
+
+
+@pytest.mark.parametrize("L,seed", [((16, 16, 16, 16), 1601), ((24, 12, 8, 6), 2402)])
+def test_fp32_update_forms_reach_the_same_maximum(L, seed):
+    """The fused and the two-kernel FP32 update both reach theta < 1e-15 on the
+    input's orbit with the oracle's F (the FP32 phases differ by FP32 rounding
+    only; the FP64 finish removes it)."""
+    U = inputs.rough_gauge_field(L, 0.3, seed)
+    ref = orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=5000)
+    with lgf.Lattice(L, mixed=True) as lat:
+        for fused in (True, False):
+            lat.set_fp32_update(fused)
+            lat.set_links(U)
+            r = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+            assert r["converged"] and r["theta"] < 1e-15 and r["iters_fp32"] > 0
+            assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+            np.testing.assert_allclose(orc.gauge_transform(L, U, lat.get_gauge()), lat.get_links(), atol=1e-13)
+        assert lat._lib.lgf_set_fp32_update(lat._h, 2) == lgf.LGF_ERR_ARG
 
 
 def test_mixed_max_iter_in_fp32_phase_keeps_progress():
