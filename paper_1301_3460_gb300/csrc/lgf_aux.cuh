@@ -175,8 +175,8 @@ static __global__ void k_unpack_full(int V, const double2* __restrict__ g, doubl
 
 // plane-wise FFT along x and y of the four fields, in place on Fd (stand-alone
 // stage; one block per xy-plane, the plane tile in shared memory)
-template <typename T, bool INV>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xy_fft(Lat d, vec2_t<T>* __restrict__ Fd)
+template <typename T, bool INV, int LMAX>
+__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_xy_fft(Lat d, vec2_t<T>* __restrict__ Fd)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
@@ -184,35 +184,35 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xy_fft(Lat d, vec2_t
     const int rsx = plane_rsx(d), fs = plane_fs(d);
     vec2_t<T>* base = Fd + s0;
     if (INV) {
-        plane_y_lines<T, true>(d, base, V, Lx, sm, fs, rsx);
+        plane_y_lines<T, true, LMAX>(d, base, V, Lx, sm, fs, rsx);
         __syncthreads();
-        tile_x_lines<T, true>(d, sm);
+        tile_x_lines<T, true, LMAX>(d, sm);
         __syncthreads();
         block_copy<4, vec2_t<T>>(
             4 * P,
             [&](int i) {
-                const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
+                const int f = (int)fdiv((unsigned)i, d.dP), xy = i - f * P, y = (int)fdiv((unsigned)xy, d.dLx), x = xy - y * Lx;
                 return sm[f * fs + y * rsx + x];
             },
             [&](int i, vec2_t<T> v) {
-                const int f = i / P, xy = i - f * P;
+                const int f = (int)fdiv((unsigned)i, d.dP), xy = i - f * P;
                 base[(size_t)f * V + xy] = v;
             });
     } else {
         block_copy<8, vec2_t<T>>(
             4 * P,
             [&](int i) {
-                const int f = i / P, xy = i - f * P;
+                const int f = (int)fdiv((unsigned)i, d.dP), xy = i - f * P;
                 return base[(size_t)f * V + xy];
             },
             [&](int i, vec2_t<T> v) {
-                const int f = i / P, xy = i - f * P, y = xy / Lx, x = xy - y * Lx;
+                const int f = (int)fdiv((unsigned)i, d.dP), xy = i - f * P, y = (int)fdiv((unsigned)xy, d.dLx), x = xy - y * Lx;
                 sm[f * fs + y * rsx + x] = v;
             });
         __syncthreads();
-        tile_x_lines<T, false>(d, sm);
+        tile_x_lines<T, false, LMAX>(d, sm);
         __syncthreads();
-        plane_y_lines<T, false>(d, sm, fs, rsx, base, V, Lx);
+        plane_y_lines<T, false, LMAX>(d, sm, fs, rsx, base, V, Lx);
     }
 }
 

@@ -136,7 +136,7 @@ bool make_shape(const Lat& d, size_t elem, int nt_xy, int nt_zt, int xw, Shape* 
 {
     if (nt_xy < 32 || nt_xy > 256 || nt_xy % 32 || nt_zt < 32 || nt_zt > 256 || nt_zt % 32) return false;
     if (plane_tile_bytes(d, elem) > kTileBudget) return false;
-    if (xw < 1 || d.L[0] % xw) return false;
+    if (xw < 1 || (xw & (xw - 1)) || d.L[0] % xw) return false;  // a power of two dividing Lx
     if (pencil_tile_bytes(d, xw, elem) > kTileBudget) return false;
     sh->nt_xy = nt_xy;
     sh->nt_zt = nt_zt;
@@ -375,12 +375,13 @@ int build_tables(lgf_ctx* c)
 {
     size_t n = 0;
     for (int mu = 0; mu < 4; mu++) n += c->L[mu];
-    const size_t bytes = n * (sizeof(double2) + sizeof(float2) + sizeof(double));
+    const size_t bytes = n * (sizeof(double2) + sizeof(float2) + sizeof(double) + sizeof(float));
     CKR(alloc(&c->tables, bytes));
     std::vector<unsigned char> h(bytes);
     double2* t64 = reinterpret_cast<double2*>(h.data());
     float2* t32 = reinterpret_cast<float2*>(h.data() + n * sizeof(double2));
     double* s2 = reinterpret_cast<double*>(h.data() + n * (sizeof(double2) + sizeof(float2)));
+    float* s2f = reinterpret_cast<float*>(h.data() + n * (sizeof(double2) + sizeof(float2) + sizeof(double)));
     const double two_pi = 6.283185307179586476925286766559;
     const double pi = 3.14159265358979323846264338327950;
     size_t off = 0;
@@ -394,6 +395,7 @@ int build_tables(lgf_ctx* c)
             t32[off + m] = make_float2((float)cos(a), (float)-sin(a));
             const double sv = sin(pi * m / L);
             s2[off + m] = 4.0 * sv * sv;
+            s2f[off + m] = (float)s2[off + m];
             if (s2[off + m] > mx) mx = s2[off + m];
         }
         c->tb.p2max += mx;
@@ -403,6 +405,8 @@ int build_tables(lgf_ctx* c)
         c->tb.s2[mu] = reinterpret_cast<const double*>(base + n * (sizeof(double2) + sizeof(float2))) + off;
         off += L;
     }
+    c->tb.s2f = reinterpret_cast<const float*>(reinterpret_cast<unsigned char*>(c->tables) +
+                                               n * (sizeof(double2) + sizeof(float2) + sizeof(double)));
     CK(cudaMemcpy(c->tables, h.data(), bytes, cudaMemcpyHostToDevice));
     // p2max/(p2(k) V) for every momentum, in both precisions
     const size_t Vs = (size_t)c->V;
@@ -440,6 +444,7 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
     d.V = c->V;
     d.P = dims[0] * dims[1];
     d.nplanes = dims[2] * dims[3];
+    lat_set_divisors(d);
     d.ne = (flags & LGF_LINKS18) ? 9 : (flags & LGF_LINKS8) ? 4 : 6;
     c->lat32 = d;
     c->lat32.ne = 6;

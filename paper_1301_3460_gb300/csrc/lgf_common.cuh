@@ -134,6 +134,29 @@ __device__ __forceinline__ void rebuild8(cx<T> a01, cx<T> a02, cx<T> a10, T th0,
 
 // ---------------------------------------------------------------- lattice
 
+// Division by a run-time constant d (1 <= d < 2^16) as a multiply-high and a
+// shift, exact for numerators 0 <= n < 2^31: s = ceil(log2 d),
+// m = floor(2^32 (2^s - d) / d) + 1, n / d = (umulhi(n, m) + n) >> s.
+struct FastDiv {
+    unsigned m, s, d;
+};
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d)
+{
+    unsigned s = 0;
+    while ((1u << s) < d) s++;
+    const unsigned long long m = ((1ull << 32) * ((1ull << s) - d)) / d + 1ull;
+    return FastDiv{(unsigned)m, s, d};
+}
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned hi = __umulhi(n, f.m);
+#else
+    const unsigned hi = (unsigned)(((unsigned long long)n * f.m) >> 32);
+#endif
+    return (unsigned)(((unsigned long long)hi + n) >> f.s);
+}
+
 // Site index s = x + Lx*(y + Ly*(z + Lz*t)).  An xy-plane is the Lx*Ly block of
 // one (z, t); plane index p = z + Lz*t.
 struct Lat {
@@ -145,7 +168,16 @@ struct Lat {
     int ne;        // complex entries stored per link: 6 (rows 0,1; row 2 rebuilt on load),
                    // 9 (row 2 kept as written, the rebuild done once when stored) or
                    // 4 (the 8-real form, FP64 only: u01, u02, u10, phases of u00 and u20)
+    FastDiv dLx, dLy, dP;  // division by Lx, Ly and Lx*Ly
 };
+
+// the division helpers of a lattice descriptor (call after L is set)
+inline void lat_set_divisors(Lat& d)
+{
+    d.dLx = make_fastdiv((unsigned)d.L[0]);
+    d.dLy = make_fastdiv((unsigned)d.L[1]);
+    d.dP = make_fastdiv((unsigned)(d.L[0] * d.L[1]));
+}
 
 __device__ __forceinline__ int site_shift(const Lat& d, int s, int c_mu, int mu, int dir)
 {

@@ -475,9 +475,22 @@ template <typename T, int L> __device__ __forceinline__ void line_inv(cx<T>* v, 
 #endif
 
 // Run f(std::integral_constant<int, L>) for the run-time line length L (one of
-// the supported lengths); returns false for any other value.
-template <typename F> __host__ __device__ __forceinline__ bool with_length(int L, F&& f)
+// the supported lengths up to LMAX); returns false for any other value.
+template <int LMAX = 128, typename F> __host__ __device__ __forceinline__ bool with_length(int L, F&& f)
 {
+    if (L > LMAX) return false;
+    if constexpr (LMAX <= 32) {
+        switch (L) {
+        case 4: f(std::integral_constant<int, 4>{}); return true;
+        case 6: f(std::integral_constant<int, 6>{}); return true;
+        case 8: f(std::integral_constant<int, 8>{}); return true;
+        case 12: f(std::integral_constant<int, 12>{}); return true;
+        case 16: f(std::integral_constant<int, 16>{}); return true;
+        case 24: f(std::integral_constant<int, 24>{}); return true;
+        case 32: f(std::integral_constant<int, 32>{}); return true;
+        default: return false;
+        }
+    }
     switch (L) {
     case 4: f(std::integral_constant<int, 4>{}); return true;
     case 6: f(std::integral_constant<int, 6>{}); return true;

@@ -31,17 +31,19 @@ __device__ __forceinline__ int ld_flag(const int* p) { return *(const volatile i
 
 // ---------------------------------------------------------------- tiles and line passes
 
-// Occupancy floor of the tiled FFT kernels: FP32 kernels (bound by memory
-// latency) keep two blocks of 256 threads per SM, FP64 kernels (bound by the
-// FP64 pipe, which a few warps keep busy) may use every register.
-template <typename T> constexpr int kTileMinBlocks = sizeof(T) == 4 ? 2 : 1;
+// Occupancy floor of the tiled FFT kernels, compiled for line lengths up to
+// LMAX: FP32 kernels (bound by memory latency) keep two blocks of 256 threads per
+// SM, three when every line is at most 32 long; FP64 kernels (bound by the FP64
+// pipe, which a few warps keep busy) may use every register.
+template <typename T, int LMAX> constexpr int kTileMinBlocks = sizeof(T) == 4 ? (LMAX <= 32 ? 3 : 2) : 1;
 
 // Shared-memory tiles.  The xy-plane tile holds the four fields of one plane as
 // [f][y][x] with row stride Lx + 1 (odd, so that the rows of consecutive lanes
 // start in different banks) and field stride Ly (Lx + 1).  The z,t pencil tile
 // of xw x-columns holds [t][kz][xi] with row stride rs = Lz xw, padded by xw when
 // xw is narrower than one shared-memory wavefront (then consecutive t fall in
-// different banks), followed by the pencil's multipliers [kt][kz][xi].
+// different banks), followed by the pencil's multipliers [kt][kz][xi] (FP64) or
+// the tables they are computed from (FP32).
 __host__ __device__ inline int plane_rsx(const Lat& d) { return d.L[0] + 1; }
 __host__ __device__ inline int plane_fs(const Lat& d) { return d.L[1] * (d.L[0] + 1); }
 __host__ __device__ inline size_t plane_smem_bytes(const Lat& d, size_t elem) { return 4 * (size_t)plane_fs(d) * elem; }
@@ -49,10 +51,14 @@ __host__ __device__ inline int pencil_rs(const Lat& d, int xw, size_t elem)
 {
     return (xw * (int)elem < 128 ? d.L[2] + 1 : d.L[2]) * xw;
 }
-// the pencil tile and, after it, the pencil's multipliers (xw Lz Lt reals of elem/2 bytes)
+// the pencil tile and, after it, FP64: the pencil's multipliers (xw Lz Lt
+// doubles); FP32: the four tables of 4 sin^2(pi k / L) the multipliers are
+// computed from
 __host__ __device__ inline size_t pencil_smem_bytes(const Lat& d, int xw, size_t elem)
 {
-    return (size_t)d.L[3] * pencil_rs(d, xw, elem) * elem + (size_t)xw * d.L[2] * d.L[3] * (elem / 2);
+    const size_t tile = (size_t)d.L[3] * pencil_rs(d, xw, elem) * elem;
+    if (elem == 8) return tile + (size_t)(d.L[0] + d.L[1] + d.L[2] + d.L[3]) * sizeof(float);
+    return tile + (size_t)xw * d.L[2] * d.L[3] * sizeof(double);
 }
 
 // dst[i] = src(i) for i < n over the block, K loads in flight per thread before
@@ -135,14 +141,14 @@ __device__ __forceinline__ void lines_accel(int nlines, LD ld, MUL mul, ST st)
 }
 
 // The x-lines (rows) of the four fields of a plane tile, in place.
-template <typename T, bool INV>
+template <typename T, bool INV, int LMAX>
 __device__ __forceinline__ void tile_x_lines(const Lat& d, vec2_t<T>* sm)
 {
     const int Ly = d.L[1], rsx = plane_rsx(d), fs = plane_fs(d);
-    with_length(d.L[0], [&](auto Lc) {
+    with_length<LMAX>(d.L[0], [&](auto Lc) {
         constexpr int L = decltype(Lc)::value;
         auto row = [&](int l) {
-            const int f = l / Ly, y = l - f * Ly;
+            const int f = (int)fdiv((unsigned)l, d.dLy), y = l - f * Ly;
             return sm + f * fs + y * rsx;
         };
         lines_pass<T, L, INV>(
@@ -154,22 +160,22 @@ __device__ __forceinline__ void tile_x_lines(const Lat& d, vec2_t<T>* sm)
 // The y-lines (columns) of the four fields of a plane: loaded from src (the
 // tile, or the plane's fields in global memory, [f][y][x] with field stride
 // src_fs and row stride src_rs), transformed, stored to dst likewise.
-template <typename T, bool INV>
+template <typename T, bool INV, int LMAX>
 __device__ __forceinline__ void plane_y_lines(const Lat& d, const vec2_t<T>* src, int src_fs, int src_rs,
                                               vec2_t<T>* dst, int dst_fs, int dst_rs)
 {
     // offsets stay 32-bit: four fields of V sites, V < 2^31 / 24
     const int Lx = d.L[0];
-    with_length(d.L[1], [&](auto Lc) {
+    with_length<LMAX>(d.L[1], [&](auto Lc) {
         constexpr int L = decltype(Lc)::value;
         lines_pass<T, L, INV>(
             4 * Lx,
             [&](int l, int e) {
-                const int f = l / Lx, x = l - f * Lx;
+                const int f = (int)fdiv((unsigned)l, d.dLx), x = l - f * Lx;
                 return ldv<T>(src + (f * src_fs + e * src_rs + x));
             },
             [&](int l, int e, cx<T> v) {
-                const int f = l / Lx, x = l - f * Lx;
+                const int f = (int)fdiv((unsigned)l, d.dLx), x = l - f * Lx;
                 st<T>(dst + (f * dst_fs + e * dst_rs + x), v);
             });
     });
@@ -362,8 +368,8 @@ __global__ void __launch_bounds__(256) k_ah_init(Lat d, const vec2_t<T>* __restr
 // fields), theta and F reduced in FP64; with FFT, the forward transform along x
 // (rows of the plane tile) and y (columns, stored straight to Fd), else Delta
 // itself to Fd.  Shared memory: the plane tile (FFT only).
-template <typename T, bool FFT>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const vec2_t<T>* __restrict__ AH, const T* __restrict__ Fs,
+template <typename T, bool FFT, int LMAX>
+__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_delta(Lat d, const vec2_t<T>* __restrict__ AH, const T* __restrict__ Fs,
                                                vec2_t<T>* __restrict__ Fd, double* __restrict__ partials, Ctl* ctl,
                                                double2* hist)
 {
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const v
 #pragma unroll 2
     for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
         const int s = s0 + xy;
-        const int y = xy / Lx, x = xy - y * Lx;
+        const int y = (int)fdiv((unsigned)xy, d.dLx), x = xy - y * Lx;
         const int c[4] = {x, y, z, t};
         int sb[4];
 #pragma unroll
@@ -415,83 +421,101 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_delta(Lat d, const v
     reduce_theta_F(th, fsum, partials, ctl, hist, V);
     if (FFT) {
         __syncthreads();
-        tile_x_lines<T, false>(d, sm);
+        tile_x_lines<T, false, LMAX>(d, sm);
         __syncthreads();
-        plane_y_lines<T, false>(d, sm, fs, rsx, Fd + s0, V, Lx);
+        plane_y_lines<T, false, LMAX>(d, sm, fs, rsx, Fd + s0, V, Lx);
     }
 }
 
 // ---------------------------------------------------------------- k_zt
 
 // One block per (x-chunk of xw columns, y, field); the fields arrive transformed
-// along x and y, so x and y are the momenta kx, ky.  The pencil's multipliers
-// p2max/(p2(k) V) (zero mode removed; mult is the table of them, site-indexed by
-// momentum, never null) are staged in shared memory; z-lines are read from Fd
-// into registers and transformed forward, stored to the pencil tile
-// [t][kz][xi]; each t-line is transformed forward, multiplied by the
-// accelerator and transformed back; the z-lines are transformed back and
-// written to Fd.
-template <typename T>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_zt(Lat d, int xw, vec2_t<T>* __restrict__ Fd, const Ctl* ctl,
-                                            const T* __restrict__ mult)
+// along x and y, so x and y are the momenta kx, ky.  The accelerator
+// p2max/(p2(k) V), zero mode removed, comes in FP64 from mult (the table of
+// multipliers, site-indexed by momentum), staged in shared memory for the
+// pencil; in FP32 it is computed from the FP32 tables s2f of 4 sin^2(pi k/L)
+// (with alpha/2 folded in, see k_xyinv_g).  z-lines are read from Fd into
+// registers and transformed forward, stored to the pencil tile [t][kz][xi]; each
+// t-line is transformed forward, multiplied by the accelerator and transformed
+// back; the z-lines are transformed back and written to Fd.
+template <typename T, int LMAX>
+__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_zt(Lat d, int xw, vec2_t<T>* __restrict__ Fd,
+                                                                     const Ctl* ctl, const double* __restrict__ mult,
+                                                                     const float* __restrict__ s2f, double p2max)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
     if (ld_flag(&ctl->phase_done)) return;
-    const int Lz = d.L[2], Lt = d.L[3];
+    const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2], Lt = d.L[3];
     const int P = d.P;  // offsets stay 32-bit (V < 2^31 / 24)
     const int rs = pencil_rs(d, xw, sizeof(vec2_t<T>));
-    const int c0 = (int)blockIdx.x * xw + d.L[0] * (int)blockIdx.y;  // (kx0, ky)
+    const int xs = __ffs(xw) - 1;  // xw is a power of two
+    const int x0 = (int)blockIdx.x * xw, ky = (int)blockIdx.y;
+    const int c0 = x0 + Lx * ky;  // (kx0, ky)
     vec2_t<T>* g = Fd + (size_t)blockIdx.z * d.V + c0;
-    T* msm = reinterpret_cast<T*>(sm + Lt * rs);
-    {
-        // FP32: the step's alpha/2 is folded in here, so that the FP64 g builder
-        // (k_xyinv_g<float, float>) receives alpha/2 Delta~ and saves its multiplies
-        const T hs = sizeof(T) == 4 ? (T)(0.5 * ctl->alpha) : (T)1;
-        const T* mrow = mult + c0;
-        block_copy<8, T>(
+    // FP64: the pencil's multipliers [kt][kz][xi]; FP32: the tables sx, sy, sz, st
+    double* m64 = reinterpret_cast<double*>(sm + Lt * rs);
+    float* t32 = reinterpret_cast<float*>(sm + Lt * rs);
+    float hc = 0.f;
+    if constexpr (sizeof(T) == 8) {
+        const double* mrow = mult + c0;
+        block_copy<8, double>(
             xw * Lz * Lt,
             [&](int i) {
-                const int zt = i / xw, xi = i - zt * xw;
+                const int zt = i >> xs, xi = i & (xw - 1);
                 return __ldg(mrow + (xi + P * zt));
             },
-            [&](int i, T v) { msm[i] = v * hs; });
+            [&](int i, double v) { m64[i] = v; });
+    } else {
+        // alpha/2 p2max / V; the g builder of the FP32 phase then takes the field as
+        // alpha/2 Delta~
+        hc = (float)(0.5 * ctl->alpha * p2max / (double)d.V);
+        block_copy<4, float>(Lx + Ly + Lz + Lt, [&](int i) { return __ldg(s2f + i); },
+                             [&](int i, float v) { t32[i] = v; });
     }
     // z forward: lines (xi, t)
-    with_length(Lz, [&](auto Lc) {
+    with_length<LMAX>(Lz, [&](auto Lc) {
         constexpr int L = decltype(Lc)::value;
         lines_pass<T, L, false>(
             xw * Lt,
             [&](int l, int e) {
-                const int tt = l / xw, xi = l - tt * xw;
+                const int tt = l >> xs, xi = l & (xw - 1);
                 return ldv<T>(g + (xi + P * (e + L * tt)));
             },
             [&](int l, int e, cx<T> v) {
-                const int tt = l / xw, xi = l - tt * xw;
+                const int tt = l >> xs, xi = l & (xw - 1);
                 st<T>(sm + tt * rs + e * xw + xi, v);
             });
     });
     __syncthreads();
     // t forward, accelerator, t inverse: lines (xi, kz)
-    with_length(Lt, [&](auto Lc) {
+    with_length<LMAX>(Lt, [&](auto Lc) {
         constexpr int L = decltype(Lc)::value;
         lines_accel<T, L>(
             xw * Lz, [&](int l, int e) { return ldv<T>(sm + e * rs + l); },
-            [&](int l, int k) { return msm[l + xw * Lz * k]; },
+            [&](int l, int k) -> T {
+                if constexpr (sizeof(T) == 8) {
+                    return m64[l + xw * Lz * k];
+                } else {
+                    const int kz = l >> xs, xi = l & (xw - 1);
+                    const float p2 = t32[x0 + xi] + t32[Lx + ky] + t32[Lx + Ly + kz] + t32[Lx + Ly + Lz + k];
+                    return p2 > 0.f ? __fdividef(hc, p2) : 0.f;
+                }
+            },
             [&](int l, int e, cx<T> v) { st<T>(sm + e * rs + l, v); });
     });
     __syncthreads();
     // z inverse: lines (xi, t), back to Fd
-    with_length(Lz, [&](auto Lc) {
+    with_length<LMAX>(Lz, [&](auto Lc) {
         constexpr int L = decltype(Lc)::value;
         lines_pass<T, L, true>(
             xw * Lt,
             [&](int l, int e) {
-                const int tt = l / xw, xi = l - tt * xw;
+                const int tt = l >> xs, xi = l & (xw - 1);
                 return ldv<T>(sm + tt * rs + e * xw + xi);
             },
             [&](int l, int e, cx<T> v) {
-                const int tt = l / xw, xi = l - tt * xw;
+                const int tt = l >> xs, xi = l & (xw - 1);
                 st<T>(g + (xi + P * (e + L * tt)), v);
             });
     });
@@ -561,8 +585,8 @@ __device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>
 // One block per xy-plane: inverse transform along y (columns read from Fd) and x
 // (rows of the plane tile), then g = reunit(1 + alpha/2 Delta~) by row
 // Gram-Schmidt in FP64 whatever T is; g stored as TG.
-template <typename T, typename TG>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
+template <typename T, typename TG, int LMAX>
+__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
                                                  vec2_t<TG>* __restrict__ g, const Ctl* ctl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -571,12 +595,12 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T>) k_xyinv_g(Lat d, const
     const int P = d.P, V = d.V, Lx = d.L[0];
     const int s0 = blockIdx.x * P;
     const int rsx = plane_rsx(d), fs = plane_fs(d);
-    plane_y_lines<T, true>(d, Fd + s0, V, Lx, sm, fs, rsx);
+    plane_y_lines<T, true, LMAX>(d, Fd + s0, V, Lx, sm, fs, rsx);
     __syncthreads();
-    tile_x_lines<T, true>(d, sm);
+    tile_x_lines<T, true, LMAX>(d, sm);
     __syncthreads();
     for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
-        const int y = xy / Lx, x = xy - y * Lx;
+        const int y = (int)fdiv((unsigned)xy, d.dLx), x = xy - y * Lx;
         const int o = y * rsx + x;
         vec2_t<T> f0 = sm[o], f1 = sm[fs + o], f2 = sm[2 * fs + o], f3 = sm[3 * fs + o];
         // X = 1 + (alpha/2) Delta~ ; rows 0 and 1 (FP32 fields arrive already

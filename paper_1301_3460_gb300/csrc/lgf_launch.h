@@ -15,8 +15,9 @@ struct Tables {
     const float2* tw32[4];
     const double* s2[4];
     double p2max;
-    const double* mult64;  // p2max/(p2(k) V) per momentum, or null (then computed in the kernel)
+    const double* mult64;  // p2max/(p2(k) V) per momentum (site-indexed)
     const float* mult32;
+    const float* s2f;      // the four tables 4 sin^2(pi k / L_mu) in FP32, one after the other
 };
 
 // launch shape of the tiled FFT kernels of one precision

@@ -8,9 +8,11 @@
 
 namespace lgf {
 
-template <typename T> inline const T* mult_of(const Tables& tb);
-template <> inline const double* mult_of<double>(const Tables& tb) { return tb.mult64; }
-template <> inline const float* mult_of<float>(const Tables& tb) { return tb.mult32; }
+// Line-length classes of the tiled kernels: every length (LMAX 128), and in FP32
+// also a variant for lattices whose lines are all at most 32 long, which needs
+// fewer registers (more warps per SM)
+template <typename T> inline bool small_plane(const Lat& d) { return sizeof(T) == 4 && d.L[0] <= 32 && d.L[1] <= 32; }
+template <typename T> inline bool small_pencil(const Lat& d) { return sizeof(T) == 4 && d.L[2] <= 32 && d.L[3] <= 32; }
 
 
 template <typename T> inline size_t xy_smem(const Lat& d) { return plane_smem_bytes(d, sizeof(vec2_t<T>)); }
@@ -38,22 +40,36 @@ template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh)
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
     if ((size_t)optin < xy_smem<T>(d) + 1024 || (size_t)optin < zt_smem<T>(d, sh)) return cudaErrorInvalidValue;
-    if ((e = allow_max_smem(k_delta<T, true>, optin))) return e;
-    if ((e = allow_max_smem(k_delta<T, false>, optin))) return e;
-    if ((e = allow_max_smem(k_xyinv_g<T, T>, optin))) return e;
-    if ((e = allow_max_smem(k_xy_fft<T, false>, optin))) return e;
-    if ((e = allow_max_smem(k_xy_fft<T, true>, optin))) return e;
-    return allow_max_smem(k_zt<T>, optin);
+    if ((e = allow_max_smem(k_delta<T, true, 128>, optin))) return e;
+    if ((e = allow_max_smem(k_delta<T, false, 128>, optin))) return e;
+    if ((e = allow_max_smem(k_xyinv_g<T, T, 128>, optin))) return e;
+    if ((e = allow_max_smem(k_xy_fft<T, false, 128>, optin))) return e;
+    if ((e = allow_max_smem(k_xy_fft<T, true, 128>, optin))) return e;
+    if ((e = allow_max_smem(k_zt<T, 128>, optin))) return e;
+    if constexpr (sizeof(T) == 4) {
+        if ((e = allow_max_smem(k_delta<T, true, 32>, optin))) return e;
+        if ((e = allow_max_smem(k_xyinv_g<T, T, 32>, optin))) return e;
+        if ((e = allow_max_smem(k_xy_fft<T, false, 32>, optin))) return e;
+        if ((e = allow_max_smem(k_xy_fft<T, true, 32>, optin))) return e;
+        if ((e = allow_max_smem(k_zt<T, 32>, optin))) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
 void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* AH, const T* Fs,
                   vec2_t<T>* Fd, double* partials, Ctl* ctl, double2* hist, bool fft)
 {
-    if (fft)
-        k_delta<T, true><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
-    else
-        k_delta<T, false><<<d.nplanes, sh.nt_xy, 0, s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+    if (!fft)
+        k_delta<T, false, 128><<<d.nplanes, sh.nt_xy, 0, s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+    else if constexpr (sizeof(T) == 4) {
+        if (small_plane<T>(d))
+            k_delta<T, true, 32><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+        else
+            k_delta<T, true, 128><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+    } else {
+        k_delta<T, true, 128><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+    }
 }
 
 template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const vec2_t<T>* U, vec2_t<T>* AH, T* Fs)
@@ -65,14 +81,26 @@ template <typename T>
 void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl)
 {
     const dim3 grid(d.L[0] / sh.xw, d.L[1], 4);
-    k_zt<T><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, mult_of<T>(tb));
+    if constexpr (sizeof(T) == 4) {
+        if (small_pencil<T>(d)) {
+            k_zt<T, 32><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tb.mult64, tb.s2f, tb.p2max);
+            return;
+        }
+    }
+    k_zt<T, 128><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tb.mult64, tb.s2f, tb.p2max);
 }
 
 template <typename T>
 void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* Fd,
                     vec2_t<T>* g, const Ctl* ctl)
 {
-    k_xyinv_g<T, T><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl);
+    if constexpr (sizeof(T) == 4) {
+        if (small_plane<T>(d)) {
+            k_xyinv_g<T, T, 32><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl);
+            return;
+        }
+    }
+    k_xyinv_g<T, T, 128><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl);
 }
 
 template <typename T> void launch_build_g(const Lat& d, cudaStream_t s, const vec2_t<T>* Fd, vec2_t<T>* g, const Ctl* ctl)
@@ -84,10 +112,19 @@ template <typename T>
 void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, bool inv)
 {
     const size_t sm = xy_smem<T>(d);
+    if constexpr (sizeof(T) == 4) {
+        if (small_plane<T>(d)) {
+            if (inv)
+                k_xy_fft<T, true, 32><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
+            else
+                k_xy_fft<T, false, 32><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
+            return;
+        }
+    }
     if (inv)
-        k_xy_fft<T, true><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
+        k_xy_fft<T, true, 128><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
     else
-        k_xy_fft<T, false><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
+        k_xy_fft<T, false, 128><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
 }
 
 template <typename T>

@@ -79,6 +79,7 @@ extern "C" int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in,
     d.V = (int)V;
     d.P = dims[0] * dims[1];
     d.nplanes = dims[2] * dims[3];
+    lat_set_divisors(d);
     // FFT tiles in shared memory: the four fields of an xy-plane, and one z,t
     // pencil of up to four x-columns
     if (plane_tile_bytes(d, sizeof(double2)) > kTileBudget) return LGF_ERR_UNSUPPORTED_DIMS;
