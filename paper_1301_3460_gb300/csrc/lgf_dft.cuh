@@ -326,6 +326,13 @@ template <typename T> __host__ __device__ constexpr int line_lanes(int L)
 }
 template <typename T> __host__ __device__ constexpr int line_vals(int L) { return L / line_lanes<T>(L); }
 
+// lanes per line of a pass that holds one transform at a time (a forward or an
+// inverse alone): FP32 lines up to 32 values fit one lane there
+template <typename T> __host__ __device__ constexpr int pass_lanes(int L)
+{
+    return (sizeof(T) == 4 && L <= 32) ? 1 : line_lanes<T>(L);
+}
+
 __host__ __device__ constexpr bool line_length_ok(int L)
 {
     return L == 4 || L == 6 || L == 8 || L == 12 || L == 16 || L == 24 || L == 32 || L == 48 || L == 64 ||
@@ -335,14 +342,13 @@ __host__ __device__ constexpr bool line_length_ok(int L)
 // Position (0..L-1) of the value a lane holds: before the forward transform
 // (and after the inverse) element tau + T j; after the forward (and before the
 // inverse) frequency r + R bitrev_T(tau).
-template <typename T, int L> __host__ __device__ __forceinline__ int line_pos_x(int tau, int j)
+template <typename T, int L, int NL = line_lanes<T>(L)> __host__ __device__ __forceinline__ int line_pos_x(int tau, int j)
 {
-    return tau + line_lanes<T>(L) * j;
+    return tau + NL * j;
 }
-template <typename T, int L> __host__ __device__ __forceinline__ int line_pos_k(int tau, int r)
+template <typename T, int L, int NL = line_lanes<T>(L)> __host__ __device__ __forceinline__ int line_pos_k(int tau, int r)
 {
-    constexpr int Tl = line_lanes<T>(L);
-    return r + line_vals<T>(L) * bitrev_n(tau, ilog2(Tl));
+    return r + (L / NL) * bitrev_n(tau, ilog2(NL));
 }
 
 // w_L^(tau E) (forward; conjugate for the inverse) for the run-time lane index
@@ -359,9 +365,10 @@ template <typename T, int L, int Tl, int E, bool INV> __host__ __device__ __forc
 }
 
 // steps 1-2 of the forward line transform in one lane (step 1 alone for T = 1)
-template <typename T, int L> __host__ __device__ __forceinline__ void line_fwd_local(cx<T>* v, int tau)
+template <typename T, int L, int NL = line_lanes<T>(L)>
+__host__ __device__ __forceinline__ void line_fwd_local(cx<T>* v, int tau)
 {
-    constexpr int Tl = line_lanes<T>(L), R = L / Tl;
+    constexpr int Tl = NL, R = L / Tl;
     dft<T, R, false>(v);
     if constexpr (Tl > 1) {
         sfor<1, R>([&](auto r) { v[r.value] = cmul(v[r.value], lane_root<T, L, Tl, r.value, false>(tau)); });
@@ -369,9 +376,10 @@ template <typename T, int L> __host__ __device__ __forceinline__ void line_fwd_l
 }
 
 // the inverse's last two steps: conjugate twiddles, then the R-point inverse codelet
-template <typename T, int L> __host__ __device__ __forceinline__ void line_inv_local(cx<T>* v, int tau)
+template <typename T, int L, int NL = line_lanes<T>(L)>
+__host__ __device__ __forceinline__ void line_inv_local(cx<T>* v, int tau)
 {
-    constexpr int Tl = line_lanes<T>(L), R = L / Tl;
+    constexpr int Tl = NL, R = L / Tl;
     if constexpr (Tl > 1) {
         sfor<1, R>([&](auto r) { v[r.value] = cmul(v[r.value], lane_root<T, L, Tl, r.value, true>(tau)); });
     }
@@ -445,10 +453,10 @@ template <typename T> __device__ __forceinline__ cx<T> shfl_xor(cx<T> a, int d)
 
 // Whole line transforms on the device.  Lanes of one line sit W = 32 / T lanes
 // apart in the warp (lane = tau W + w); every lane of the warp must call.
-template <typename T, int L> __device__ __forceinline__ void line_fwd(cx<T>* v, int tau)
+template <typename T, int L, int NL = line_lanes<T>(L)> __device__ __forceinline__ void line_fwd(cx<T>* v, int tau)
 {
-    constexpr int Tl = line_lanes<T>(L), R = L / Tl, W = 32 / Tl;
-    line_fwd_local<T, L>(v, tau);
+    constexpr int Tl = NL, R = L / Tl, W = 32 / Tl;
+    line_fwd_local<T, L, NL>(v, tau);
     if constexpr (Tl > 1) {
         sfor<0, ilog2(Tl)>([&](auto s) {
             constexpr int h = Tl >> (1 + s.value);
@@ -459,9 +467,9 @@ template <typename T, int L> __device__ __forceinline__ void line_fwd(cx<T>* v, 
     }
 }
 
-template <typename T, int L> __device__ __forceinline__ void line_inv(cx<T>* v, int tau)
+template <typename T, int L, int NL = line_lanes<T>(L)> __device__ __forceinline__ void line_inv(cx<T>* v, int tau)
 {
-    constexpr int Tl = line_lanes<T>(L), R = L / Tl, W = 32 / Tl;
+    constexpr int Tl = NL, R = L / Tl, W = 32 / Tl;
     if constexpr (Tl > 1) {
         sfor<0, ilog2(Tl)>([&](auto s) {
             constexpr int h = 1 << s.value;
@@ -470,7 +478,7 @@ template <typename T, int L> __device__ __forceinline__ void line_inv(cx<T>* v, 
             for (int r = 0; r < R; r++) v[r] = xsum(v[r], shfl_xor(v[r], h * W), tau, h);
         });
     }
-    line_inv_local<T, L>(v, tau);
+    line_inv_local<T, L, NL>(v, tau);
 }
 #endif
 

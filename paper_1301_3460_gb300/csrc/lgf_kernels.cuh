@@ -86,12 +86,12 @@ __device__ __forceinline__ void block_copy(int n, SRC src, DST dst)
 // is read through ld(line, position) and written through st(line, position,
 // value), positions 0..L-1 along the line in natural order (time in, frequency
 // out for the forward transform; the reverse for the inverse).  The lanes of a
-// line (line_lanes(L) of them) work together, so every thread of the block
+// line (pass_lanes(L) of them) work together, so every thread of the block
 // calls this with the same nlines; lines are dealt out a warp at a time.
 template <typename T, int L, bool INV, typename LD, typename ST>
 __device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st)
 {
-    constexpr int Tl = line_lanes<T>(L), R = L / Tl, W = 32 / Tl;
+    constexpr int Tl = pass_lanes<T>(L), R = L / Tl, W = 32 / Tl;
     const int lane = (int)threadIdx.x & 31, tau = lane / W, w = lane - tau * W;
     const int step = ((int)blockDim.x >> 5) * W;
     for (int l0 = ((int)threadIdx.x >> 5) * W; l0 < nlines; l0 += step) {
@@ -100,12 +100,14 @@ __device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st)
         const int lc = ok ? l : l0;
         cx<T> v[R];
 #pragma unroll
-        for (int j = 0; j < R; j++) v[j] = ld(lc, INV ? line_pos_k<T, L>(tau, j) : line_pos_x<T, L>(tau, j));
-        if constexpr (INV) line_inv<T, L>(v, tau);
-        else line_fwd<T, L>(v, tau);
+        for (int j = 0; j < R; j++)
+            v[j] = ld(lc, INV ? line_pos_k<T, L, Tl>(tau, j) : line_pos_x<T, L, Tl>(tau, j));
+        if constexpr (INV) line_inv<T, L, Tl>(v, tau);
+        else line_fwd<T, L, Tl>(v, tau);
         if (ok) {
 #pragma unroll
-            for (int j = 0; j < R; j++) st(l, INV ? line_pos_x<T, L>(tau, j) : line_pos_k<T, L>(tau, j), v[j]);
+            for (int j = 0; j < R; j++)
+                st(l, INV ? line_pos_x<T, L, Tl>(tau, j) : line_pos_k<T, L, Tl>(tau, j), v[j]);
         }
     }
 }
