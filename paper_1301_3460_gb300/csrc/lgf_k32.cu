@@ -10,11 +10,7 @@ int update_grid(int V) { return (V + 255) / 256; }
 void launch_update_delta32(const Lat& d, cudaStream_t s, const float2* Uin, float2* Uout, float2* G, const float2* g,
                            Ctl* ctl, float2* Fd, double* partials, double2* hist)
 {
-    // whole x-rows per block (Lx divides 32; 256 threads hold 256 / Lx rows)
-    if (32 % d.L[0] == 0)
-        k_update_delta<float, true><<<update_grid(d.V), 256, 0, s>>>(d, Uin, Uout, G, g, ctl, Fd, partials, hist);
-    else
-        k_update_delta<float, false><<<update_grid(d.V), 256, 0, s>>>(d, Uin, Uout, G, g, ctl, Fd, partials, hist);
+    k_update_delta<float><<<update_grid(d.V), 256, 0, s>>>(d, Uin, Uout, G, g, ctl, Fd, partials, hist);
 }
 
 void launch_delta_links32(const Lat& d, cudaStream_t s, const float2* U, float2* Fd, double* partials, Ctl* ctl,

@@ -768,107 +768,50 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
 //   space), theta and F of the new links reduced in FP64, the loop state updated.
 // Uin and Uout are different buffers: a thread reads its neighbours' old links,
 // which their own threads replace in the same launch.
-// ROWS: Lx divides 32 and a block of 256 threads holds whole x-rows, so that the
-// x-entering link's part comes from the lane of x - 1 by a warp shuffle and the
-// y-entering one from the previous row of the block through shared memory
-// (recomputed only in the block's first row and at y = 0); otherwise every
-// entering link is recomputed.
-template <typename T> __device__ __forceinline__ void add_entering(cx<T>* D, const cx<T>* a)
-{
-#pragma unroll
-    for (int k = 0; k < 4; k++) D[k] = D[k] + a[k];
-}
 template <typename T>
-__device__ __forceinline__ void entering_ah(const Lat& d, const vec2_t<T>* __restrict__ Uin,
-                                            const vec2_t<T>* __restrict__ g, int mu, int sb, const cx<T>* gx,
-                                            cx<T>* a)
-{
-    cx<T> u[9], gb[9], w[9];
-    load_link<T>(Uin, d.V, d.ne, mu, sb, u);
-    load_g<T>(g, d.V, sb, gb);
-    link_gug(gb, u, gx, w);
-    ah_pack(w, a);
-}
-
-template <typename T, bool ROWS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_update_delta(
     Lat d, const vec2_t<T>* __restrict__ Uin, vec2_t<T>* __restrict__ Uout, vec2_t<T>* __restrict__ G,
     const vec2_t<T>* __restrict__ g, Ctl* ctl, vec2_t<T>* __restrict__ Fd, double* __restrict__ partials,
     double2* hist)
 {
-    __shared__ vec2_t<T> ahy[ROWS ? 4 * 256 : 1];
     if (ld_flag(&ctl->phase_done)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->iter += 1;
         if (ctl->phase == 0) ctl->iter_phase0 += 1;
     }
-    const int V = d.V, Lx = d.L[0];
-    const int tid = threadIdx.x;
-    const int s = blockIdx.x * blockDim.x + tid;
-    const bool in = s < V;
-    const int sc = in ? s : V - 1;  // a valid site for threads past the end (results unused)
-    int c[4];
-    site_coords(d, sc, c);
-    cx<T> gx[9];
-    load_g<T>(g, V, sc, gx);
-    cx<T> D[4], ax[4], ay[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) D[k] = mk<T>(0, 0);
-    T f = 0;
-    // the links leaving x
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        cx<T> u[9], gn[9], w[9], a[4];
-        load_link<T>(Uin, V, d.ne, mu, sc, u);
-        load_g<T>(g, V, site_shift(d, sc, c[mu], mu, +1), gn);
-        link_gug(gx, u, gn, w);
-        if (in) store_link<T>(Uout, V, d.ne, mu, s, w);
-        ah_pack(w, a);
-#pragma unroll
-        for (int k = 0; k < 4; k++) D[k] = D[k] - a[k];
-        if (mu == 0)
-#pragma unroll
-            for (int k = 0; k < 4; k++) ax[k] = a[k];
-        if (mu == 1)
-#pragma unroll
-            for (int k = 0; k < 4; k++) ay[k] = a[k];
-        f += w[0].re + w[4].re + w[8].re;
-    }
-    // the links entering x
-    if constexpr (ROWS) {
-#pragma unroll
-        for (int k = 0; k < 4; k++) ahy[k * 256 + tid] = vec2_t<T>{ay[k].re, ay[k].im};
-        const int lane = tid & 31;
-        const int src = (lane & ~(Lx - 1)) | ((lane + Lx - 1) & (Lx - 1));  // the lane of x - 1 in the row
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            ax[k] = cx<T>{__shfl_sync(0xffffffffu, ax[k].re, src), __shfl_sync(0xffffffffu, ax[k].im, src)};
-        add_entering(D, ax);
-        __syncthreads();
-        if (tid >= Lx && c[1] > 0) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const vec2_t<T> v = ahy[k * 256 + tid - Lx];
-                ay[k] = cx<T>{v.x, v.y};
-            }
-        } else {
-            entering_ah<T>(d, Uin, g, 1, site_shift(d, sc, c[1], 1, -1), gx, ay);
-        }
-        add_entering(D, ay);
-    } else {
-        entering_ah<T>(d, Uin, g, 0, site_shift(d, sc, c[0], 0, -1), gx, ax);
-        add_entering(D, ax);
-        entering_ah<T>(d, Uin, g, 1, site_shift(d, sc, c[1], 1, -1), gx, ay);
-        add_entering(D, ay);
-    }
-#pragma unroll
-    for (int mu = 2; mu < 4; mu++) {
-        cx<T> a[4];
-        entering_ah<T>(d, Uin, g, mu, site_shift(d, sc, c[mu], mu, -1), gx, a);
-        add_entering(D, a);
-    }
+    const int V = d.V;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double th = 0.0, fsum = 0.0;
-    if (in) {
+    if (s < V) {
+        int c[4];
+        site_coords(d, s, c);
+        cx<T> gx[9];
+        load_g<T>(g, V, s, gx);
+        cx<T> D[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) D[k] = mk<T>(0, 0);
+        T f = 0;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            cx<T> u[9], gn[9], w[9], a[4];
+            // the link leaving x
+            load_link<T>(Uin, V, d.ne, mu, s, u);
+            load_g<T>(g, V, site_shift(d, s, c[mu], mu, +1), gn);
+            link_gug(gx, u, gn, w);
+            store_link<T>(Uout, V, d.ne, mu, s, w);
+            ah_pack(w, a);
+#pragma unroll
+            for (int k = 0; k < 4; k++) D[k] = D[k] - a[k];
+            f += w[0].re + w[4].re + w[8].re;
+            // the link entering x from x - mu
+            const int sb = site_shift(d, s, c[mu], mu, -1);
+            load_link<T>(Uin, V, d.ne, mu, sb, u);
+            load_g<T>(g, V, sb, gn);
+            link_gug(gn, u, gx, w);
+            ah_pack(w, a);
+#pragma unroll
+            for (int k = 0; k < 4; k++) D[k] = D[k] + a[k];
+        }
         if (G != nullptr) gauge_accumulate<T>(G, V, s, gx);
 #pragma unroll
         for (int k = 0; k < 4; k++) st<T>(Fd + (size_t)k * V + s, D[k]);
