@@ -355,7 +355,7 @@ def run_ours(args, dims):
         latm.set_switch_tol(1e-6)
         latm.set_links(dev[1])
         msm = latm.time_kernels(args.alpha, n_iter=8, precision=32)
-        per32 = roofline.per_site(dims, 32)
+        per32 = roofline.per_site(dims, 32, fused32=False)
         mixed["kernels_fp32"] = {k: {"ms": msm[k], "gbs": per32[k]["bytes"] * V / msm[k] / 1e6,
                                      "gflops": per32[k]["flops"] * V / msm[k] / 1e6} for k in msm}
         latm.close()
@@ -923,12 +923,10 @@ def run_kernels(args, dims):
         lat.set_links(U)
         if not args.no_autotune:
             lat.autotune()
-        # FP64, FP32 with the update fused with Delta (the default), FP32 in the
-        # two-kernel form
-        for name, prec, fused in (("fp64", 64, True), ("fp32", 32, True), ("fp32_unfused", 32, False)):
+        # FP64, FP32 in the two-kernel form (the default), FP32 with the update
+        # fused with Delta
+        for name, prec, fused in (("fp64", 64, False), ("fp32", 32, False), ("fp32_fused", 32, True)):
             lat.set_fp32_update(fused)
-            if fused is False and not args.no_autotune:
-                lat.autotune()
             if args.warmup:
                 lat.time_kernels(args.alpha, n_iter=args.warmup, precision=prec)
             ms = lat.time_kernels(args.alpha, n_iter=max(1, args.steps), precision=prec)
@@ -937,7 +935,7 @@ def run_kernels(args, dims):
                              "hbm_frac_of_measured": per[k]["bytes"] * V / ms[k] / 1e6 / hbm,
                              "gflops": per[k]["flops"] * V / ms[k] / 1e6} for k in ms}
             out[name + "_iteration_ms"] = sum(ms.values())
-        lat.set_fp32_update(True)
+        lat.set_fp32_update(False)
     print(json.dumps(out), flush=True)
     return 0
 

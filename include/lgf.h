@@ -178,14 +178,14 @@ int lgf_set_switch_tol(lgf_ctx* ctx, double switch_tol);
 int lgf_set_fp32_refresh(lgf_ctx* ctx, int every);
 
 /*
- * LGF_MIXED: the form of the FP32 phase's update.  fused = 1 (default): one
- * kernel updates the links and forms Delta, theta and F of the new links,
- * recomputing the anti-Hermitian part of each link that enters a site from its
- * neighbour's old link (the links alternate between two FP32 buffers).  fused =
- * 0: the update writes each new link's packed anti-Hermitian part and Re Tr, and
- * a separate kernel forms Delta from them (the FP64 phase's form).  Results agree
- * to FP32 rounding; the setting only changes the kernels' work.  Other values:
- * LGF_ERR_ARG.
+ * LGF_MIXED: the form of the FP32 phase's update.  fused = 1: one kernel
+ * updates the links and forms Delta, theta and F of the new links, recomputing
+ * the anti-Hermitian part of each link that enters a site from its neighbour's
+ * old link (the links alternate between two FP32 buffers).  fused = 0 (default):
+ * the update writes each new link's packed anti-Hermitian part and Re Tr, and a
+ * separate kernel forms Delta from them (the FP64 phase's form; the faster of
+ * the two on GB300).  Results agree to FP32 rounding; the setting only changes
+ * the kernels' work.  Other values: LGF_ERR_ARG.
  */
 int lgf_set_fp32_update(lgf_ctx* ctx, int fused);
 

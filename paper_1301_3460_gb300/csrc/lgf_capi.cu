@@ -93,7 +93,7 @@ struct lgf_ctx {
     float2* g32 = nullptr;
     float2* AH32 = nullptr;   // FP32 phase without the fused update: packed anti-Hermitian
     float* Fs32 = nullptr;    // parts and Re Tr handed from the update to the Delta kernel
-    bool fused32 = true;      // FP32 phase: update fused with Delta (links recomputed) or not
+    bool fused32 = false;     // FP32 phase: update fused with Delta (links recomputed) or not
     void* Fd = nullptr;       // [4][V] double2 (the FP32 phase uses the front half as float2)
     double2* AH64 = nullptr;  // [4][4][V] packed anti-Hermitian parts of the links
     double* Fs64 = nullptr;   // [V] Re Tr of the four links of a site

@@ -384,6 +384,54 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_delta(Lat d, c
     const int z = plane % d.L[2], t = plane / d.L[2];
     const int rsx = plane_rsx(d), fs = plane_fs(d);
     double th = 0.0, fsum = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: two sites (x, x+1) per thread, every part loaded as a pair of sites
+        // in one 16-byte load (x even; the neighbours along y, z, t are pairs too,
+        // and along x the pair's first neighbour is x - 1, its second x itself)
+        const float4* AH4 = reinterpret_cast<const float4*>(AH);
+        const int V2 = V / 2;
+#pragma unroll 1
+        for (int xy = 2 * threadIdx.x; xy < P; xy += 2 * blockDim.x) {
+            const int s = s0 + xy;
+            const int y = (int)fdiv((unsigned)xy, d.dLx), x = xy - y * Lx;
+            const int c[4] = {x, y, z, t};
+            int sb[4];
+#pragma unroll
+            for (int mu = 1; mu < 4; mu++) sb[mu] = site_shift(d, s, c[mu], mu, -1);
+            sb[0] = site_shift(d, s, x, 0, -1);
+            const float2 fs2 = __ldg(reinterpret_cast<const float2*>(Fs) + s / 2);
+            fsum += (double)fs2.x + (double)fs2.y;
+            cx<float> D0[4], D1[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                // site x: ah_x(x-1) - ah_x(x); site x+1: ah_x(x) - ah_x(x+1)
+                const float4 b = __ldg(AH4 + (size_t)k * V2 + s / 2);
+                const float2 a = __ldg(AH + (size_t)k * V + sb[0]);
+                D0[k] = mk<float>(a.x - b.x, a.y - b.y);
+                D1[k] = mk<float>(b.x - b.z, b.y - b.w);
+            }
+#pragma unroll
+            for (int mu = 1; mu < 4; mu++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float4 a = __ldg(AH4 + (size_t)(mu * 4 + k) * V2 + sb[mu] / 2);
+                    const float4 b = __ldg(AH4 + (size_t)(mu * 4 + k) * V2 + s / 2);
+                    D0[k] = D0[k] + mk<float>(a.x - b.x, a.y - b.y);
+                    D1[k] = D1[k] + mk<float>(a.z - b.z, a.w - b.w);
+                }
+            th += (double)theta_site(D0) + (double)theta_site(D1);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (FFT) {
+                    st<float>(reinterpret_cast<float2*>(sm) + k * fs + y * rsx + x, D0[k]);
+                    st<float>(reinterpret_cast<float2*>(sm) + k * fs + y * rsx + x + 1, D1[k]);
+                } else {
+                    st<float>(reinterpret_cast<float2*>(Fd) + (size_t)k * V + s, D0[k]);
+                    st<float>(reinterpret_cast<float2*>(Fd) + (size_t)k * V + s + 1, D1[k]);
+                }
+            }
+        }
+    } else {
 #pragma unroll 2
     for (int xy = threadIdx.x; xy < P; xy += blockDim.x) {
         const int s = s0 + xy;
@@ -419,6 +467,7 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_delta(Lat d, c
 #pragma unroll
             for (int k = 0; k < 4; k++) st<T>(Fd + (size_t)k * V + s, D[k]);
         }
+    }
     }
     reduce_theta_F(th, fsum, partials, ctl, hist, V);
     if (FFT) {

@@ -214,7 +214,7 @@ class Lattice:
         _check(self._lib.lgf_set_fp32_refresh(self._h, int(every)), "lgf_set_fp32_refresh")
 
     def set_fp32_update(self, fused: bool):
-        """FP32 phase: update fused with Delta (True) or the two-kernel form (False)."""
+        """FP32 phase: update fused with Delta (True) or the two-kernel form (False, the default)."""
         _check(self._lib.lgf_set_fp32_update(self._h, 1 if fused else 0), "lgf_set_fp32_update")
 
     def set_links(self, U):

@@ -22,7 +22,7 @@ FP64 path, per site (V sites per launch):
                 G: rebuild (42) + one product (132).
 FP32 kernels move half the bytes of every array they keep in FP32 (links, G, g,
 fields, packed parts, multiplier); their flop counts are the same.  The FP32
-phase's default form fuses Delta into the update (fused=True):
+phase's other form fuses Delta into the update (fused32=True):
   delta_xyfft   the forward x,y FFT alone: reads and writes the 4 fields (32 + 32 B).
   update        reads links, g, G; writes links, G and Delta: 192 + 72 + 48 + 192 +
                 48 + 32 B (the neighbours' links and g that it also reads are other
@@ -50,7 +50,7 @@ import math
 KERNELS = ("delta_xyfft", "zt_fft_accel", "xyifft_g", "update")
 
 
-def per_site(dims, precision: int = 64, fused32: bool = True) -> dict:
+def per_site(dims, precision: int = 64, fused32: bool = False) -> dict:
     Lx, Ly, Lz, Lt = (int(v) for v in dims)
     w = 1.0 if precision == 64 else 0.5
     lxy = math.log2(Lx * Ly)
@@ -73,7 +73,7 @@ def per_site(dims, precision: int = 64, fused32: bool = True) -> dict:
     }
 
 
-def per_iteration(dims, precision: int = 64, fused32: bool = True) -> dict:
+def per_iteration(dims, precision: int = 64, fused32: bool = False) -> dict:
     V = 1
     for v in dims:
         V *= int(v)
