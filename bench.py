@@ -62,10 +62,11 @@ def parse():
     ap.add_argument("--no-cpu-fix", action="store_true", help="skip the oracle's full-size fix in cpu_baseline")
     ap.add_argument("--no-48", action="store_true", help="skip the 48^4 FP64-vs-mixed leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 58-lattice ensemble leg")
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson", "kernels"],
+    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson", "kernels", "probe"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble; "
                          "wilson: Wilson-action configuration generation (heat bath + overrelaxation); "
-                         "kernels: the iteration kernels launched one by one (FP64 and FP32), per-kernel times")
+                         "kernels: the iteration kernels launched one by one (FP64 and FP32), per-kernel times; "
+                         "probe: the FP64 and FP32 FMA rates of the GPU (the FP64 kernels' arithmetic ceiling)")
     ap.add_argument("--no-autotune", action="store_true", help="--workload kernels: default launch shapes")
     ap.add_argument("--beta", type=float, default=6.0, help="coupling of --workload wilson")
     ap.add_argument("--switch-tol", type=float, default=1e-6,
@@ -940,8 +941,35 @@ def run_kernels(args, dims):
     return 0
 
 
+def run_probe(args):
+    """FP64 and FP32 FMA rates (best of --steps launches after --warmup), with the
+    SM clock sampled during the launches."""
+    import torch
+
+    from paper_1301_3460_gb300 import lgf
+
+    torch.cuda.set_device(0)
+    clocks = Clocks(0)
+    clocks.start()
+    out = {"metric": "FMA rate (an FMA = 2 flops)", "unit": "GFLOP/s", "per_sm_clock_nominal": {
+        "fp64": FP64_PEAK_GFLOPS, "note": "152 SMs x 2 FP64 FMA per cycle x 2 flops x 2.07 GHz"}}
+    for prec, n in ((64, 20000), (32, 400000)):
+        for _ in range(args.warmup):
+            lgf.probe_fma(prec, n)
+        runs = [lgf.probe_fma(prec, n) for _ in range(max(1, args.steps))]
+        best = max(runs, key=lambda r: r["gflops"])
+        out["fp%d" % prec] = {"gflops": best["gflops"], "ms": best["ms"], "n_iter": n,
+                              "all_gflops": [r["gflops"] for r in runs]}
+    out["clocks"] = clocks.stop()
+    out["fp64_frac_of_nominal"] = out["fp64"]["gflops"] / FP64_PEAK_GFLOPS
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "probe":
+        return run_probe(args)
     if args.workload == "kernels":
         return run_kernels(args, tuple(int(v) for v in args.dims.split(",")))
     if args.workload == "ensemble":

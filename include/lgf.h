@@ -209,21 +209,34 @@ int lgf_build_g(lgf_ctx* ctx, const double* Dt_in, double alpha, double* g_out, 
  * with CUDA events around each launch, and write to ms[4] the median over the
  * iterations of the duration (milliseconds) of (0) the Delta + x,y FFT kernel, (1) the z,t FFT +
  * accelerator kernel, (2) the inverse x,y FFT + g kernel, (3) the update
- * kernel.  precision 64 times the FP64 kernels; 32 the FP32 kernels (mixed
- * contexts only; they start from an FP32 copy of the stored links).  The stored
- * links advance by n_iter updates (precision 64) or are left as they were (32).
+ * kernel.  precision 64 times the FP64 kernels; 32 the FP32 kernels of the
+ * form lgf_set_fp32_update chose (mixed contexts only; they start from an FP32
+ * copy of the stored links; with the fused update, (0) is the x,y FFT alone and
+ * (3) the update fused with Delta).  The stored links advance by n_iter updates
+ * (precision 64) or are left as they were (32).
  */
 int lgf_time_kernels(lgf_ctx* ctx, double alpha, int n_iter, int precision, double* ms);
 
 /*
  * lgf_autotune: choose the launch shapes of the shared-memory FFT kernels (block
- * sizes, fields per x,y transform, x-columns per z,t pencil) for this lattice by
+ * sizes of the plane and pencil kernels, x-columns per z,t pencil) for this lattice by
  * timing the candidates on the stored links; both precisions of a mixed
  * context.  The choice is cached for the process by extents and precision.
  * Needs lgf_set_links first (LGF_ERR_STATE otherwise).  Changes no result
  * beyond rounding.
  */
 int lgf_autotune(lgf_ctx* ctx);
+
+/*
+ * lgf_probe_fma (instrumentation, no counterpart in the paper): the FMA rate of
+ * the current GPU in FP64 (precision 64) or FP32 (32), from one launch of 8
+ * independent FMA chains of n_iter steps per thread over 8 blocks of 256 threads
+ * per SM, timed with CUDA events after a short warm-up launch; *gflops counts
+ * an FMA as two flops, *ms (may be NULL) is the launch time.  The FP64 rate is
+ * the arithmetic ceiling of the FP64 iteration kernels.  Allocates a small
+ * output buffer; blocks until done.
+ */
+int lgf_probe_fma(int precision, int n_iter, double* gflops, double* ms);
 
 /*
  * Batched ensembles (no counterpart in the paper's single-lattice runs): n

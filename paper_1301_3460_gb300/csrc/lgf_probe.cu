@@ -1,0 +1,64 @@
+// lgf_probe_fma: the FMA rate of this GPU in FP64 or FP32, the arithmetic peak
+// that the FP64 kernels of the gauge fixing are measured against (their bound is
+// the FP64 pipe, not memory).  Instrumentation; not a step of the method.
+//
+// Each thread runs 8 independent FMA chains of n_iter steps on values that stay
+// bounded (x <- x * a + b with |a| < 1), so the pipe sees no dependency stalls,
+// and writes one value so the work cannot be dropped.  The grid fills every SM
+// several times over.
+#include <cuda_runtime.h>
+
+#include "../../include/lgf.h"
+
+namespace {
+
+template <typename T> __global__ void __launch_bounds__(256) k_fma_probe(int n_iter, T a, T b, T* out)
+{
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    for (int i = 0; i < n_iter; i++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = fma(x[k], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T> int probe(int n_iter, double* gflops, double* ms_out)
+{
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LGF_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LGF_ERR_CUDA;
+    const int blocks = nsm * 8, threads = 256;
+    T* out = nullptr;
+    if (cudaMalloc((void**)&out, (size_t)blocks * threads * sizeof(T)) != cudaSuccess) return LGF_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fma_probe<T><<<blocks, threads>>>(n_iter / 10 + 1, (T)0.999, (T)1e-4, out);  // warm-up
+    cudaEventRecord(e0);
+    k_fma_probe<T><<<blocks, threads>>>(n_iter, (T)0.999, (T)1e-4, out);
+    cudaEventRecord(e1);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return LGF_ERR_CUDA;
+    const double flops = 2.0 * 8.0 * (double)n_iter * blocks * threads;
+    *gflops = flops / (ms * 1e-3) / 1e9;
+    if (ms_out) *ms_out = ms;
+    return LGF_OK;
+}
+
+}  // namespace
+
+extern "C" int lgf_probe_fma(int precision, int n_iter, double* gflops, double* ms)
+{
+    if (!gflops || n_iter < 1 || (precision != 64 && precision != 32)) return LGF_ERR_ARG;
+    return precision == 64 ? probe<double>(n_iter, gflops, ms) : probe<float>(n_iter, gflops, ms);
+}

@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
             "lgf_time_kernels": ([P, D, I, I, DP], I),
             "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
             "lgf_autotune": ([P], I),
+            "lgf_probe_fma": ([I, I, DP, DP], I),
             "lgf_step_fwd": ([P, D, P, P], I),
             "lgf_step_bwd": ([P, D, P, P], I),
             "lgf_gluon_pmin": ([P, DP, DP], I),
@@ -318,6 +319,14 @@ def _autotune(self) -> None:
 
 
 Lattice.autotune = _autotune
+
+
+def probe_fma(precision: int = 64, n_iter: int = 100000) -> dict:
+    """FMA rate (GFLOP/s, an FMA counted as two flops) of the current GPU in FP64 or FP32."""
+    lib = load()
+    gf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.lgf_probe_fma(int(precision), int(n_iter), ctypes.byref(gf), ctypes.byref(ms)), "lgf_probe_fma")
+    return dict(gflops=gf.value, ms=ms.value, precision=precision, n_iter=n_iter)
 
 
 def _step_fwd(self, U_in, alpha: float = 0.08):
