@@ -953,7 +953,7 @@ def run_probe(args):
     clocks.start()
     out = {"metric": "FMA rate (an FMA = 2 flops)", "unit": "GFLOP/s", "per_sm_clock_nominal": {
         "fp64": FP64_PEAK_GFLOPS, "note": "152 SMs x 2 FP64 FMA per cycle x 2 flops x 2.07 GHz"}}
-    for prec, n in ((64, 20000), (32, 400000)):
+    for prec, n in ((64, 10000), (32, 200000)):
         for _ in range(args.warmup):
             lgf.probe_fma(prec, n)
         runs = [lgf.probe_fma(prec, n) for _ in range(max(1, args.steps))]

@@ -229,7 +229,7 @@ int lgf_autotune(lgf_ctx* ctx);
 
 /*
  * lgf_probe_fma (instrumentation, no counterpart in the paper): the FMA rate of
- * the current GPU in FP64 (precision 64) or FP32 (32), from one launch of 8
+ * the current GPU in FP64 (precision 64) or FP32 (32), from one launch of 16
  * independent FMA chains of n_iter steps per thread over 8 blocks of 256 threads
  * per SM, timed with CUDA events after a short warm-up launch; *gflops counts
  * an FMA as two flops, *ms (may be NULL) is the launch time.  The FP64 rate is

@@ -176,7 +176,7 @@ static __global__ void k_unpack_full(int V, const double2* __restrict__ g, doubl
 // plane-wise FFT along x and y of the four fields, in place on Fd (stand-alone
 // stage; one block per xy-plane, the plane tile in shared memory)
 template <typename T, bool INV, int LMAX>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_xy_fft(Lat d, vec2_t<T>* __restrict__ Fd)
+__global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_xy_fft(Lat d, vec2_t<T>* __restrict__ Fd)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);

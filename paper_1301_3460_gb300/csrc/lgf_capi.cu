@@ -131,10 +131,11 @@ struct lgf_ctx {
 namespace {
 
 // Shared-memory FFT tiles: the four fields of an xy-plane, and one z,t pencil of
-// xw x-columns; thread counts a multiple of 32 up to 256.
+// xw x-columns; thread counts a multiple of 32 up to 128 (FP64) or 256 (FP32).
 bool make_shape(const Lat& d, size_t elem, int nt_xy, int nt_zt, int xw, Shape* sh)
 {
-    if (nt_xy < 32 || nt_xy > 256 || nt_xy % 32 || nt_zt < 32 || nt_zt > 256 || nt_zt % 32) return false;
+    const int ntmax = elem == sizeof(double2) ? 128 : 256;  // the tile kernels' launch bounds
+    if (nt_xy < 32 || nt_xy > ntmax || nt_xy % 32 || nt_zt < 32 || nt_zt > ntmax || nt_zt % 32) return false;
     if (plane_tile_bytes(d, elem) > kTileBudget) return false;
     if (xw < 1 || (xw & (xw - 1)) || d.L[0] % xw) return false;  // a power of two dividing Lx
     if (pencil_tile_bytes(d, xw, elem) > kTileBudget) return false;

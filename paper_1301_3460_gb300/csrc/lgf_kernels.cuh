@@ -35,7 +35,10 @@ __device__ __forceinline__ int ld_flag(const int* p) { return *(const volatile i
 // LMAX: FP32 kernels (bound by memory latency) keep two blocks of 256 threads per
 // SM, three when every line is at most 32 long; FP64 kernels (bound by the FP64
 // pipe, which a few warps keep busy) may use every register.
-template <typename T, int LMAX> constexpr int kTileMinBlocks = sizeof(T) == 4 ? (LMAX <= 32 ? 3 : 2) : 1;
+template <typename T, int LMAX> constexpr int kTileMinBlocks = sizeof(T) == 4 ? (LMAX <= 32 ? 3 : 2) : (LMAX <= 32 ? 3 : 1);
+// FP64 tiles run at most 128 threads per block (a 32-point line per thread needs
+// ~160 registers; three such blocks per SM keep 12 warps on the FP64 pipe)
+template <typename T> constexpr int kTileMaxThreads = sizeof(T) == 8 ? 128 : 256;
 
 // Shared-memory tiles.  The xy-plane tile holds the four fields of one plane as
 // [f][y][x] with row stride Lx + 1 (odd, so that the rows of consecutive lanes
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(256) k_ah_init(Lat d, const vec2_t<T>* __restr
 // (rows of the plane tile) and y (columns, stored straight to Fd), else Delta
 // itself to Fd.  Shared memory: the plane tile (FFT only).
 template <typename T, bool FFT, int LMAX>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_delta(Lat d, const vec2_t<T>* __restrict__ AH, const T* __restrict__ Fs,
+__global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_delta(Lat d, const vec2_t<T>* __restrict__ AH, const T* __restrict__ Fs,
                                                vec2_t<T>* __restrict__ Fd, double* __restrict__ partials, Ctl* ctl,
                                                double2* hist)
 {
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_delta(Lat d, c
 // t-line is transformed forward, multiplied by the accelerator and transformed
 // back; the z-lines are transformed back and written to Fd.
 template <typename T, int LMAX>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_zt(Lat d, int xw, vec2_t<T>* __restrict__ Fd,
+__global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_zt(Lat d, int xw, vec2_t<T>* __restrict__ Fd,
                                                                      const Ctl* ctl, const double* __restrict__ mult,
                                                                      const float* __restrict__ s2f, double p2max)
 {
@@ -637,7 +640,7 @@ __device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>
 // (rows of the plane tile), then g = reunit(1 + alpha/2 Delta~) by row
 // Gram-Schmidt in FP64 whatever T is; g stored as TG.
 template <typename T, typename TG, int LMAX>
-__global__ void __launch_bounds__(256, kTileMinBlocks<T, LMAX>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
+__global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
                                                  vec2_t<TG>* __restrict__ g, const Ctl* ctl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

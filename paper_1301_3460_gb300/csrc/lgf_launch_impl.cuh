@@ -8,10 +8,10 @@
 
 namespace lgf {
 
-// Line-length classes of the tiled kernels: every length (LMAX 128), and in FP32
-// also a variant for lattices whose lines are all at most 32 long, which needs
-// fewer registers (more warps per SM)
-template <typename T> inline bool small_plane(const Lat& d) { return sizeof(T) == 4 && d.L[0] <= 32 && d.L[1] <= 32; }
+// Line-length classes of the tiled kernels: every length (LMAX 128), and a
+// variant for planes (both precisions) and FP32 pencils whose lines are all at
+// most 32 long, which needs fewer registers (more warps per SM)
+template <typename T> inline bool small_plane(const Lat& d) { return d.L[0] <= 32 && d.L[1] <= 32; }
 template <typename T> inline bool small_pencil(const Lat& d) { return sizeof(T) == 4 && d.L[2] <= 32 && d.L[3] <= 32; }
 
 
@@ -46,11 +46,11 @@ template <typename T> cudaError_t prepare_kernels(const Lat& d, const Shape& sh)
     if ((e = allow_max_smem(k_xy_fft<T, false, 128>, optin))) return e;
     if ((e = allow_max_smem(k_xy_fft<T, true, 128>, optin))) return e;
     if ((e = allow_max_smem(k_zt<T, 128>, optin))) return e;
+    if ((e = allow_max_smem(k_delta<T, true, 32>, optin))) return e;
+    if ((e = allow_max_smem(k_xyinv_g<T, T, 32>, optin))) return e;
+    if ((e = allow_max_smem(k_xy_fft<T, false, 32>, optin))) return e;
+    if ((e = allow_max_smem(k_xy_fft<T, true, 32>, optin))) return e;
     if constexpr (sizeof(T) == 4) {
-        if ((e = allow_max_smem(k_delta<T, true, 32>, optin))) return e;
-        if ((e = allow_max_smem(k_xyinv_g<T, T, 32>, optin))) return e;
-        if ((e = allow_max_smem(k_xy_fft<T, false, 32>, optin))) return e;
-        if ((e = allow_max_smem(k_xy_fft<T, true, 32>, optin))) return e;
         if ((e = allow_max_smem(k_zt<T, 32>, optin))) return e;
     }
     return cudaSuccess;
@@ -62,14 +62,10 @@ void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t 
 {
     if (!fft)
         k_delta<T, false, 128><<<d.nplanes, sh.nt_xy, 0, s>>>(d, AH, Fs, Fd, partials, ctl, hist);
-    else if constexpr (sizeof(T) == 4) {
-        if (small_plane<T>(d))
-            k_delta<T, true, 32><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
-        else
-            k_delta<T, true, 128><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
-    } else {
+    else if (small_plane<T>(d))
+        k_delta<T, true, 32><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+    else
         k_delta<T, true, 128><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, AH, Fs, Fd, partials, ctl, hist);
-    }
 }
 
 template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const vec2_t<T>* U, vec2_t<T>* AH, T* Fs)
@@ -94,11 +90,9 @@ template <typename T>
 void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* Fd,
                     vec2_t<T>* g, const Ctl* ctl)
 {
-    if constexpr (sizeof(T) == 4) {
-        if (small_plane<T>(d)) {
-            k_xyinv_g<T, T, 32><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl);
-            return;
-        }
+    if (small_plane<T>(d)) {
+        k_xyinv_g<T, T, 32><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl);
+        return;
     }
     k_xyinv_g<T, T, 128><<<d.nplanes, sh.nt_xy, xy_smem<T>(d), s>>>(d, Fd, g, ctl);
 }
@@ -112,14 +106,12 @@ template <typename T>
 void launch_xy_fft(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, bool inv)
 {
     const size_t sm = xy_smem<T>(d);
-    if constexpr (sizeof(T) == 4) {
-        if (small_plane<T>(d)) {
-            if (inv)
-                k_xy_fft<T, true, 32><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
-            else
-                k_xy_fft<T, false, 32><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
-            return;
-        }
+    if (small_plane<T>(d)) {
+        if (inv)
+            k_xy_fft<T, true, 32><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
+        else
+            k_xy_fft<T, false, 32><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);
+        return;
     }
     if (inv)
         k_xy_fft<T, true, 128><<<d.nplanes, sh.nt_xy, sm, s>>>(d, Fd);

@@ -2,7 +2,7 @@
 // that the FP64 kernels of the gauge fixing are measured against (their bound is
 // the FP64 pipe, not memory).  Instrumentation; not a step of the method.
 //
-// Each thread runs 8 independent FMA chains of n_iter steps on values that stay
+// Each thread runs 16 independent FMA chains of n_iter steps on values that stay
 // bounded (x <- x * a + b with |a| < 1), so the pipe sees no dependency stalls,
 // and writes one value so the work cannot be dropped.  The grid fills every SM
 // several times over.
@@ -14,16 +14,16 @@ namespace {
 
 template <typename T> __global__ void __launch_bounds__(256) k_fma_probe(int n_iter, T a, T b, T* out)
 {
-    T x[8];
+    T x[16];
 #pragma unroll
-    for (int k = 0; k < 8; k++) x[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    for (int k = 0; k < 16; k++) x[k] = (T)(threadIdx.x + k) * (T)1e-3;
     for (int i = 0; i < n_iter; i++) {
 #pragma unroll
-        for (int k = 0; k < 8; k++) x[k] = fma(x[k], a, b);
+        for (int k = 0; k < 16; k++) x[k] = fma(x[k], a, b);
     }
     T s = 0;
 #pragma unroll
-    for (int k = 0; k < 8; k++) s += x[k];
+    for (int k = 0; k < 16; k++) s += x[k];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -49,7 +49,7 @@ template <typename T> int probe(int n_iter, double* gflops, double* ms_out)
     cudaEventDestroy(e1);
     cudaFree(out);
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return LGF_ERR_CUDA;
-    const double flops = 2.0 * 8.0 * (double)n_iter * blocks * threads;
+    const double flops = 2.0 * 16.0 * (double)n_iter * blocks * threads;
     *gflops = flops / (ms * 1e-3) / 1e9;
     if (ms_out) *ms_out = ms;
     return LGF_OK;
