@@ -573,9 +573,14 @@ def run_ours(args, dims):
     traffic = traffic_record(kern, dims, 64)
     roof = {"bound": "alu", "kernel": kern, "achieved": flops / sec / 1e9, "peak": FP64_PEAK_GFLOPS,
             "unit": "GFLOP/s", "frac": flops / sec / 1e9 / FP64_PEAK_GFLOPS, "traffic": traffic,
-            "peak_source": "GB300 FP64: 152 SMs x 4 flops/cycle x 2.07 GHz (1.25 TFLOP/s nominal); an FMA probe "
-                           "measured 1190 GFLOP/s",
+            "peak_source": "GB300 FP64 from unit counts and clock: 152 SMs x 2 FP64 FMA/cycle x 2 flops x 2.07 GHz "
+                           "(1.25 TFLOP/s nominal); probe_gflops is the FMA-only probe of this run "
+                           "(bench.py --workload probe)",
             "hbm_achieved_gbs": byts / sec / 1e9}
+    try:
+        roof["probe_gflops"] = lgf.probe_fma(64, 10000)["gflops"]
+    except lgf.LgfError:
+        roof["probe_gflops"] = None
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         roof["hbm_frac_of_measured"] = roof["hbm_achieved_gbs"] / float(peaks["hbm_gbs"])

@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k
 template <typename T, int LMAX>
 __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_zt(Lat d, int xw, vec2_t<T>* __restrict__ Fd,
                                                                      const Ctl* ctl, const double* __restrict__ mult,
-                                                                     const float* __restrict__ s2f, double p2max)
+                                                                     const float* __restrict__ s2f, float p2max_v)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
@@ -521,9 +521,9 @@ __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k
             },
             [&](int i, double v) { m64[i] = v; });
     } else {
-        // alpha/2 p2max / V; the g builder of the FP32 phase then takes the field as
-        // alpha/2 Delta~
-        hc = (float)(0.5 * ctl->alpha * p2max / (double)d.V);
+        // alpha/2 p2max / V (p2max_v = p2max / V); the g builder of the FP32 phase
+        // then takes the field as alpha/2 Delta~
+        hc = 0.5f * (float)ctl->alpha * p2max_v;
         block_copy<4, float>(Lx + Ly + Lz + Lt, [&](int i) { return __ldg(s2f + i); },
                              [&](int i, float v) { t32[i] = v; });
     }

@@ -79,11 +79,13 @@ void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, 
     const dim3 grid(d.L[0] / sh.xw, d.L[1], 4);
     if constexpr (sizeof(T) == 4) {
         if (small_pencil<T>(d)) {
-            k_zt<T, 32><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tb.mult64, tb.s2f, tb.p2max);
+            k_zt<T, 32><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tb.mult64, tb.s2f,
+                                                                  (float)(tb.p2max / d.V));
             return;
         }
     }
-    k_zt<T, 128><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tb.mult64, tb.s2f, tb.p2max);
+    k_zt<T, 128><<<grid, sh.nt_zt, zt_smem<T>(d, sh), s>>>(d, sh.xw, Fd, ctl, tb.mult64, tb.s2f,
+                                                           (float)(tb.p2max / d.V));
 }
 
 template <typename T>
