@@ -359,6 +359,15 @@ def run_ours(args, dims):
         per32 = roofline.per_site(dims, 32, fused32=False)
         mixed["kernels_fp32"] = {k: {"ms": msm[k], "gbs": per32[k]["bytes"] * V / msm[k] / 1e6,
                                      "gflops": per32[k]["flops"] * V / msm[k] / 1e6} for k in msm}
+        mixed["fp32_iteration_ms"] = sum(msm.values())
+        # the FP32 phase with the update fused with Delta (selectable form), same kernels timed
+        latm.set_fp32_update(True)
+        msf = latm.time_kernels(args.alpha, n_iter=8, precision=32)
+        perf = roofline.per_site(dims, 32, fused32=True)
+        mixed["kernels_fp32_fused"] = {k: {"ms": msf[k], "gbs": perf[k]["bytes"] * V / msf[k] / 1e6}
+                                       for k in msf}
+        mixed["fp32_fused_iteration_ms"] = sum(msf.values())
+        latm.set_fp32_update(False)
         latm.close()
 
     # link parametrisation: the same FP64 workload with row 2 kept in memory (18 reals)
@@ -588,6 +597,7 @@ def run_ours(args, dims):
         pass
     kernels = {k: {"ms": ms[k], "gflops": per[k]["flops"] * V / ms[k] / 1e6, "gbs": per[k]["bytes"] * V / ms[k] / 1e6}
                for k in ms}
+    kernels["fp64_iteration_ms"] = sum(ms.values())
     # the metric's "% of HBM peak": algorithmic bytes of one whole FP64 iteration at the measured rate
     try:
         hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -595,9 +605,10 @@ def run_ours(args, dims):
         hbm_iter = {"bytes_per_iteration": it_bytes, "achieved_gbs": it_bytes * value / 1e9, "peak_gbs": hbm,
                     "frac": it_bytes * value / 1e9 / hbm,
                     "note": "FP64 iteration bound by the FP64 pipe, not by HBM; see roofline"}
-        if mixed is not None and "kernels_fp32" in mixed:
-            for k, v in mixed["kernels_fp32"].items():
-                v["hbm_frac_of_measured"] = v["gbs"] / hbm
+        if mixed is not None:
+            for key in ("kernels_fp32", "kernels_fp32_fused"):
+                for k, v in mixed.get(key, {}).items():
+                    v["hbm_frac_of_measured"] = v["gbs"] / hbm
     except (OSError, ValueError, KeyError):
         hbm_iter = None
 

@@ -10,7 +10,8 @@ FP64 path, per site (V sites per launch):
                 complex) and their Re Tr sum, writes the four packed Delta
                 fields: 256 + 8 + 64 B.  Flops: Delta as 16 complex differences
                 (64), theta and F (21), x,y FFT of 4 fields (4 x 5 log2(Lx Ly)).
-  zt_fft_accel  reads the multiplier and reads/writes the 4 fields: 8 + 64 + 64 B.
+  zt_fft_accel  reads the multiplier table and reads/writes the 4 fields: 8 + 64 + 64 B
+                (FP32: the multiplier is computed from per-axis tables, 32 + 32 B).
                 Flops: forward and inverse z,t FFT of 4 fields
                 (2 x 4 x 5 log2(Lz Lt)) + scale (8).
   xyifft_g      reads the 4 fields, writes g (full 3x3): 64 + 144 B.  Flops:
@@ -58,7 +59,7 @@ def per_site(dims, precision: int = 64, fused32: bool = False) -> dict:
     if precision == 32 and fused32:
         return {
             "delta_xyfft": dict(bytes=(64 + 64) * w, flops=4 * 5 * lxy),
-            "zt_fft_accel": dict(bytes=(8 + 64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
+            "zt_fft_accel": dict(bytes=(64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
             "xyifft_g": dict(bytes=(64 + 144) * w, flops=4 * 5 * lxy + 134),
             "update": dict(bytes=(384 + 144 + 96 + 384 + 96 + 64) * w,
                            flops=4 * (42 + 2 * 132 + 42 + 12 + 2) + 4 * (42 + 2 * 132 + 42 + 12) + 42 + 132
@@ -66,7 +67,7 @@ def per_site(dims, precision: int = 64, fused32: bool = False) -> dict:
         }
     return {
         "delta_xyfft": dict(bytes=(256 + 8 + 64) * w, flops=64 + 21 + 4 * 5 * lxy),
-        "zt_fft_accel": dict(bytes=(8 + 64 + 64) * w, flops=2 * 4 * 5 * lzt + 8),
+        "zt_fft_accel": dict(bytes=(64 + 64) * w + (8 if precision == 64 else 0), flops=2 * 4 * 5 * lzt + 8),
         "xyifft_g": dict(bytes=(64 + 144) * w, flops=4 * 5 * lxy + 134),
         "update": dict(bytes=(384 + 144 + 96 + 384 + 96 + 256 + 8) * w,
                        flops=4 * (42 + 2 * 132 + 42 + 12 + 2) + 42 + 132),
