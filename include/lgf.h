@@ -239,6 +239,17 @@ int lgf_autotune(lgf_ctx* ctx);
 int lgf_probe_fma(int precision, int n_iter, double* gflops, double* ms);
 
 /*
+ * lgf_check_conversions (instrumentation, no counterpart in the paper): the
+ * integer-pipe conversions the FP32 phase's g builder uses, applied elementwise
+ * on the device: f_out[i] = d_in[i] rounded to binary32 (to nearest, ties to
+ * even), d_out[i] = f_in[i] widened to binary64 (exact).  All four are device
+ * pointers to n elements, owned by the caller; the results must equal the
+ * hardware conversions bit for bit.  n = 0 does nothing; n < 0 or a NULL pointer
+ * with n > 0 gives LGF_ERR_ARG.  Blocks until done.
+ */
+int lgf_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int n);
+
+/*
  * Batched ensembles (no counterpart in the paper's single-lattice runs): n
  * lattices of possibly different extents, fixed together by one CUDA graph
  * launch in which every lattice's device-resident loop is an independent branch,

@@ -78,6 +78,42 @@ template <typename T> __device__ __forceinline__ void st(vec2_t<T>* p, cx<T> a)
     *p = v;
 }
 
+// ---------------------------------------------------------------- precision conversions
+
+// float -> double (exact) and double -> float (round to nearest, ties to even)
+// by integer operations on the IEEE 754 encodings (binary32: sign, 8-bit
+// exponent biased by 127, 23-bit fraction; binary64: sign, 11-bit exponent
+// biased by 1023, 52-bit fraction).  On this GPU the hardware conversions issue
+// on the FP64 pipe (2 per cycle per SM); these use the integer pipe.  Finite
+// normal values of the target format take the integer path; zeros, subnormals,
+// overflow, infinities and NaNs take the hardware conversion, so every result is
+// the hardware's.
+__device__ __forceinline__ double f2d_int(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e - 1u >= 254u) return (double)f;
+    // exponent rebiased by 1023 - 127; the fraction's top 20 bits in the high
+    // word, its low 3 bits at the top of the low word
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ float d2f_int(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned E = (hi >> 20) & 0x7ffu;
+    // binary32 exponent E - 896 must lie in [1, 254]
+    if (E - 897u >= 254u) return __double2float_rn(x);
+    const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the kept 23 fraction bits
+    const unsigned rest = lo & 0x1fffffffu;                      // the 29 dropped bits
+    unsigned r = (hi & 0x80000000u) | ((E - 896u) << 23) | m23;
+    // +1 when rest > 2^28, or rest = 2^28 and m23 is odd; a carry out of the
+    // fraction increments the exponent (to infinity from the largest binade)
+    r += (rest + 0x0fffffffu + (m23 & 1u)) >> 29;
+    return __uint_as_float(r);
+}
+
 // ---------------------------------------------------------------- SU(3)
 
 // conj(a b - c d) with four fused multiply-adds per component

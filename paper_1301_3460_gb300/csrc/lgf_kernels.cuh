@@ -661,12 +661,15 @@ __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k
         // multiplied by alpha/2, in the z,t kernel)
         cx<double> X[6];
         if constexpr (sizeof(T) == 4) {
-            X[0] = mk<double>(1.0, (double)f3.x);
-            X[1] = mk<double>((double)f0.x, (double)f0.y);
-            X[2] = mk<double>((double)f1.x, (double)f1.y);
-            X[3] = mk<double>(-(double)f0.x, (double)f0.y);  // -conj(Delta01)
-            X[4] = mk<double>(1.0, (double)f3.y);
-            X[5] = mk<double>((double)f2.x, (double)f2.y);
+            // conversions on the integer pipe (f2d_int, d2f_int below): a fifth
+            // of this kernel's FP64-pipe work otherwise
+            const double a0 = f2d_int(f0.x), a1 = f2d_int(f0.y);
+            X[0] = mk<double>(1.0, f2d_int(f3.x));
+            X[1] = mk<double>(a0, a1);
+            X[2] = mk<double>(f2d_int(f1.x), f2d_int(f1.y));
+            X[3] = mk<double>(-a0, a1);  // -conj(Delta01)
+            X[4] = mk<double>(1.0, f2d_int(f3.y));
+            X[5] = mk<double>(f2d_int(f2.x), f2d_int(f2.y));
         } else {
             const double h = 0.5 * ctl->alpha;
             X[0] = mk<double>(1.0, h * f3.x);
@@ -682,8 +685,13 @@ __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k
         cx<double> gm[6];
         gram_schmidt01(X, gm);
         cx<TG> gs[9];
+        if constexpr (sizeof(TG) == 4) {
 #pragma unroll
-        for (int e = 0; e < 6; e++) gs[e] = mk<TG>((TG)gm[e].re, (TG)gm[e].im);
+            for (int e = 0; e < 6; e++) gs[e] = mk<TG>(d2f_int(gm[e].re), d2f_int(gm[e].im));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 6; e++) gs[e] = mk<TG>((TG)gm[e].re, (TG)gm[e].im);
+        }
         complete_row2(gs, gs + 6);
 #pragma unroll
         for (int e = 0; e < 9; e++) st<TG>(g + (size_t)e * V + s0 + xy, gs[e]);

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lgf.h"
+#include "lgf_common.cuh"
 
 namespace {
 
@@ -55,7 +56,25 @@ template <typename T> int probe(int n_iter, double* gflops, double* ms_out)
     return LGF_OK;
 }
 
+__global__ void k_check_conversions(const double* __restrict__ d_in, float* __restrict__ f_out,
+                                    const float* __restrict__ f_in, double* __restrict__ d_out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    f_out[i] = lgf::d2f_int(d_in[i]);
+    d_out[i] = lgf::f2d_int(f_in[i]);
+}
+
 }  // namespace
+
+extern "C" int lgf_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int n)
+{
+    if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out))) return LGF_ERR_ARG;
+    if (n == 0) return LGF_OK;
+    k_check_conversions<<<(n + 255) / 256, 256>>>(d_in, f_out, f_in, d_out, n);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return LGF_ERR_CUDA;
+    return LGF_OK;
+}
 
 extern "C" int lgf_probe_fma(int precision, int n_iter, double* gflops, double* ms)
 {

@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
             "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
             "lgf_autotune": ([P], I),
             "lgf_probe_fma": ([I, I, DP, DP], I),
+            "lgf_check_conversions": ([P, P, P, P, I], I),
             "lgf_step_fwd": ([P, D, P, P], I),
             "lgf_step_bwd": ([P, D, P, P], I),
             "lgf_gluon_pmin": ([P, DP, DP], I),
@@ -327,6 +328,25 @@ def probe_fma(precision: int = 64, n_iter: int = 100000) -> dict:
     gf, ms = ctypes.c_double(), ctypes.c_double()
     _check(lib.lgf_probe_fma(int(precision), int(n_iter), ctypes.byref(gf), ctypes.byref(ms)), "lgf_probe_fma")
     return dict(gflops=gf.value, ms=ms.value, precision=precision, n_iter=n_iter)
+
+
+def check_conversions(d_in, f_in):
+    """The integer-pipe float/double conversions of the FP32 phase's g builder,
+    applied to d_in (float64 CUDA tensor) and f_in (float32 CUDA tensor, same
+    length): returns (d_in rounded to float32, f_in widened to float64)."""
+    import torch
+
+    if not (_is_torch(d_in) and _is_torch(f_in) and d_in.is_cuda and f_in.is_cuda):
+        raise TypeError("check_conversions takes CUDA tensors")
+    if d_in.dtype != torch.float64 or f_in.dtype != torch.float32 or d_in.numel() != f_in.numel():
+        raise TypeError("check_conversions takes a float64 and a float32 tensor of the same length")
+    d_in, f_in = d_in.contiguous(), f_in.contiguous()
+    f_out = torch.empty_like(f_in)
+    d_out = torch.empty_like(d_in)
+    with torch.cuda.device(d_in.device):
+        _check(load().lgf_check_conversions(d_in.data_ptr(), f_out.data_ptr(), f_in.data_ptr(), d_out.data_ptr(),
+                                            int(d_in.numel())), "lgf_check_conversions")
+    return f_out, d_out
 
 
 def _step_fwd(self, U_in, alpha: float = 0.08):
