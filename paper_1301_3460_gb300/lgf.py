@@ -204,6 +204,7 @@ class Lattice:
         """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default)."""
         raw = getattr(stream, "cuda_stream", stream)
         _check(self._lib.lgf_set_stream(self._h, ctypes.c_void_p(raw or 0)), "lgf_set_stream")
+        self._stream = stream  # the context launches on it: keep the object alive as long as the context
 
     def set_loop_bound(self, n: int):
         """Fault injection: cap each device loop at n body runs (0: no cap)."""
