@@ -414,6 +414,7 @@ class Batch:
         if stream is not None:
             raw = getattr(stream, "cuda_stream", stream)
             _check(lib.lgf_batch_set_stream(h, ctypes.c_void_p(raw or 0)), "lgf_batch_set_stream")
+            self._stream = stream
 
     def close(self):
         if getattr(self, "_h", None):
