@@ -321,8 +321,8 @@ int lgf_gluon_pmin_bwd(lgf_ctx* ctx, double gD, double* gU);
  * 5 MiB that every GPU loading the library holds until the process exits.  Each
  * call looks up the array's device address on the current device; the first
  * call on a device (and the first after the array has moved, e.g. after
- * cudaDeviceReset) also sets kernel attributes: make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
+ * cudaDeviceReset) also sets kernel attributes.  All calls share the array and
+ * it keeps the last call's
  * contents (what must start at zero is cleared on every call); calls whose work
  * overlaps on the GPU race on it.  Returns after the stream has finished.
  */
