@@ -204,6 +204,26 @@ int lgf_accelerate(lgf_ctx* ctx, const double* Delta_in, double* Dt_out, int on_
 int lgf_build_g(lgf_ctx* ctx, const double* Dt_in, double alpha, double* g_out, int on_device);
 
 /*
+ * The same three stages as the FP32 phase of LGF_MIXED computes them (its own
+ * kernels; inputs and outputs in FP64, layouts as above), for checking that
+ * phase stage by stage against the FP64 results to FP32 accuracy.  Need a
+ * context created with LGF_MIXED, else LGF_ERR_STATE.
+ *
+ * lgf_delta32: the stored links rounded to FP32, then Delta (forward x,y
+ *   transform and back, as the phase transforms it) with theta and F reduced in
+ *   FP64.  Needs lgf_set_links first (LGF_ERR_STATE).  Overwrites the context's
+ *   FP32 links, which lgf_fix rebuilds from the FP64 links on every call.
+ * lgf_accelerate32: Delta~ of a given Delta with the FP32 transforms and FP32
+ *   multipliers p2max/(p2 V).
+ * lgf_build_g32: g = reunit(1 + alpha/2 Dt): the field rounded to FP32 and taken
+ *   through the phase's forward and inverse x,y transforms, the Gram-Schmidt in
+ *   FP64, g rounded to FP32 (row 2 rebuilt in FP32 from the rounded rows).
+ */
+int lgf_delta32(lgf_ctx* ctx, double* Delta_out, int on_device, double* theta, double* F);
+int lgf_accelerate32(lgf_ctx* ctx, const double* Delta_in, double* Dt_out, int on_device);
+int lgf_build_g32(lgf_ctx* ctx, const double* Dt_in, double alpha, double* g_out, int on_device);
+
+/*
  * lgf_time_kernels (instrumentation): run n_iter iterations of the loop body on
  * the stored links, launching the kernels one by one on the context's stream
  * with CUDA events around each launch, and write to ms[4] the median over the

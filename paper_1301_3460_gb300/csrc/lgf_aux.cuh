@@ -159,6 +159,23 @@ static __global__ void k_unpack_delta(int V, const double2* __restrict__ Fd, dou
     for (int e = 0; e < 18; e++) p[e] = m[e];
 }
 
+// n complex values from FP64 to FP32 and back, times a real scale (the FP32
+// stage entry points: their inputs and outputs are FP64)
+static __global__ void k_planes_to32(long n, const double2* __restrict__ in, float2* __restrict__ out, double scale)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 v = in[i];
+    out[i] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+}
+static __global__ void k_planes_to64(long n, const float2* __restrict__ in, double2* __restrict__ out, double scale)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 v = in[i];
+    out[i] = make_double2((double)v.x * scale, (double)v.y * scale);
+}
+
 // [9][V] planes of full matrices -> [V][3][3] complex128
 static __global__ void k_unpack_full(int V, const double2* __restrict__ g, double* __restrict__ out)
 {

@@ -1081,6 +1081,94 @@ int lgf_build_g(lgf_ctx* c, const double* Dt_in, double alpha, double* g_out, in
     return stage_out_end(c, g_out, bytes, copy);
 }
 
+// FP32-phase stage entry points: the FP32 phase's own kernels between FP64
+// inputs and outputs.  The FP32 fields occupy the front half of Fd; results are
+// widened into g64 ([9][V] double2) and unpacked from there.
+int lgf_delta32(lgf_ctx* c, double* Delta_out, int on_device, double* theta, double* F)
+{
+    if (!c) return LGF_ERR_ARG;
+    if (!c->mixed || !c->have_links) return LGF_ERR_STATE;
+    CKR(reset_stage_ctl(c));
+    float2* Fd32 = reinterpret_cast<float2*>(c->Fd);
+    // the FP32 phase's start: links rounded to FP32, Delta, theta and F, the
+    // forward x,y transform of Delta
+    launch_mixed_prep(c->stream, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl_stage);
+    launch_start32(c, c->stream, c->ctl_stage, nullptr);
+    CK(cudaGetLastError());
+    if (Delta_out) {
+        double scale = 1.0;
+        if (!c->plain) {  // back along x,y (unnormalised: P times the field)
+            launch_xy_fft<float>(c->lat32, c->sh32, c->tb, c->stream, Fd32, true);
+            scale = 1.0 / (double)c->lat.P;
+        }
+        launch_planes_to64(c->stream, 4L * c->V, Fd32, c->g64, scale);
+        const size_t bytes = (size_t)c->V * 18 * sizeof(double);
+        double* dst;
+        bool copy;
+        CKR(stage_out_begin(c, Delta_out, bytes, on_device, &dst, &copy));
+        launch_unpack_delta(c->stream, c->V, c->g64, dst);
+        CK(cudaGetLastError());
+        CKR(stage_out_end(c, Delta_out, bytes, copy));
+    }
+    CK(cudaMemcpyAsync(c->host_ctl, c->ctl_stage, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (theta) *theta = c->host_ctl->theta;
+    if (F) *F = c->host_ctl->F;
+    return LGF_OK;
+}
+
+int lgf_accelerate32(lgf_ctx* c, const double* Delta_in, double* Dt_out, int on_device)
+{
+    if (!c || !Delta_in || !Dt_out) return LGF_ERR_ARG;
+    if (!c->mixed) return LGF_ERR_STATE;
+    const size_t bytes = (size_t)c->V * 18 * sizeof(double);
+    const double* src;
+    // the FP32 z,t kernel scales by (alpha/2) p2max/(p2 V): alpha = 2 gives the
+    // accelerator itself
+    CKR(reset_stage_ctl(c, 2.0));
+    CKR(stage_in(c, Delta_in, bytes, on_device, &src));
+    float2* Fd32 = reinterpret_cast<float2*>(c->Fd);
+    launch_pack_delta(c->stream, c->V, src, c->g64);
+    launch_planes_to32(c->stream, 4L * c->V, c->g64, Fd32, 1.0);
+    launch_xy_fft<float>(c->lat32, c->sh32, c->tb, c->stream, Fd32, false);
+    launch_zt<float>(c->lat32, c->sh32, c->tb, c->stream, Fd32, c->ctl_stage);
+    launch_xy_fft<float>(c->lat32, c->sh32, c->tb, c->stream, Fd32, true);
+    launch_planes_to64(c->stream, 4L * c->V, Fd32, c->g64, 1.0);
+    CK(cudaGetLastError());
+    double* dst;
+    bool copy;
+    CKR(stage_out_begin(c, Dt_out, bytes, on_device, &dst, &copy));
+    launch_unpack_delta(c->stream, c->V, c->g64, dst);
+    CK(cudaGetLastError());
+    return stage_out_end(c, Dt_out, bytes, copy);
+}
+
+int lgf_build_g32(lgf_ctx* c, const double* Dt_in, double alpha, double* g_out, int on_device)
+{
+    if (!c || !Dt_in || !g_out) return LGF_ERR_ARG;
+    if (!c->mixed) return LGF_ERR_STATE;
+    const size_t bytes = (size_t)c->V * 18 * sizeof(double);
+    const double* src;
+    CKR(reset_stage_ctl(c, alpha));
+    CKR(stage_in(c, Dt_in, bytes, on_device, &src));
+    float2* Fd32 = reinterpret_cast<float2*>(c->Fd);
+    // the FP32 builder takes fields transformed along x,y and already multiplied
+    // by alpha/2, and its inverse x,y transform is unnormalised: rounded to FP32
+    // times alpha/(2 P), then transformed forward
+    launch_pack_delta(c->stream, c->V, src, c->g64);
+    launch_planes_to32(c->stream, 4L * c->V, c->g64, Fd32, 0.5 * alpha / (double)c->lat.P);
+    launch_xy_fft<float>(c->lat32, c->sh32, c->tb, c->stream, Fd32, false);
+    launch_xyinv_g<float>(c->lat32, c->sh32, c->tb, c->stream, Fd32, c->g32, c->ctl_stage);
+    launch_planes_to64(c->stream, 9L * c->V, c->g32, c->g64, 1.0);
+    CK(cudaGetLastError());
+    double* dst;
+    bool copy;
+    CKR(stage_out_begin(c, g_out, bytes, on_device, &dst, &copy));
+    launch_unpack_full(c->stream, c->V, c->g64, dst);
+    CK(cudaGetLastError());
+    return stage_out_end(c, g_out, bytes, copy);
+}
+
 int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double* ms)
 {
     if (!c || !ms || n_iter < 1 || !(alpha > 0)) return LGF_ERR_ARG;

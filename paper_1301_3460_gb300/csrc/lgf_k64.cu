@@ -38,6 +38,14 @@ void launch_unpack_full(cudaStream_t s, int V, const double2* g, double* out)
 {
     k_unpack_full<<<blocks(V, 256), 256, 0, s>>>(V, g, out);
 }
+void launch_planes_to32(cudaStream_t s, long n, const double2* in, float2* out, double scale)
+{
+    k_planes_to32<<<blocks(n, 256), 256, 0, s>>>(n, in, out, scale);
+}
+void launch_planes_to64(cudaStream_t s, long n, const float2* in, double2* out, double scale)
+{
+    k_planes_to64<<<blocks(n, 256), 256, 0, s>>>(n, in, out, scale);
+}
 void launch_mixed_prep(cudaStream_t s, int V, int ne, const double2* U64, float2* U32, float2* G32, const Ctl* ctl)
 {
     k_mixed_prep<<<blocks(V, 256), 256, 0, s>>>(V, ne, U64, U32, G32, ctl);

@@ -65,6 +65,9 @@ void launch_identity_rows64(cudaStream_t s, int V, double2* G);
 void launch_pack_delta(cudaStream_t s, int V, const double* in, double2* Fd);
 void launch_unpack_delta(cudaStream_t s, int V, const double2* Fd, double* out);
 void launch_unpack_full(cudaStream_t s, int V, const double2* g, double* out);
+// n complex values FP64 -> FP32 and FP32 -> FP64, times scale
+void launch_planes_to32(cudaStream_t s, long n, const double2* in, float2* out, double scale);
+void launch_planes_to64(cudaStream_t s, long n, const float2* in, double2* out, double scale);
 void launch_mixed_prep(cudaStream_t s, int V, int ne, const double2* U64, float2* U32, float2* G32, const Ctl* ctl);
 void launch_switch(cudaStream_t s, const Lat& d, const float2* G32, double2* Gs, double2* U64, double2* G64,
                    Ctl* ctl);

@@ -86,6 +86,9 @@ def load(build_if_missing: bool = True):
             "lgf_delta": ([P, P, I, DP, DP], I),
             "lgf_accelerate": ([P, P, P, I], I),
             "lgf_build_g": ([P, P, D, P, I], I),
+            "lgf_delta32": ([P, P, I, DP, DP], I),
+            "lgf_accelerate32": ([P, P, P, I], I),
+            "lgf_build_g32": ([P, P, D, P, I], I),
             "lgf_time_kernels": ([P, D, I, I, DP], I),
             "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
             "lgf_autotune": ([P], I),
@@ -255,25 +258,38 @@ class Lattice:
                                          ctypes.byref(w)), "lgf_get_history")
         return buf[: 2 * w.value].reshape(-1, 2)
 
-    def delta(self, device=None):
+    def delta(self, device=None, precision: int = 64):
+        """Delta, theta and F of the stored links; precision 32: as the FP32
+        phase of a mixed context computes them (lgf_delta32)."""
+        fn, name = self._stage_fn("lgf_delta", precision)
         out, p, dev = _out(None, (self.V, 3, 3), device)
         th, F = ctypes.c_double(), ctypes.c_double()
-        _check(self._lib.lgf_delta(self._h, p, dev, ctypes.byref(th), ctypes.byref(F)), "lgf_delta")
+        _check(fn(self._h, p, dev, ctypes.byref(th), ctypes.byref(F)), name)
         return out, th.value, F.value
 
-    def accelerate(self, D):
+    def accelerate(self, D, precision: int = 64):
+        """Delta~ of D; precision 32: with the FP32 phase's kernels (lgf_accelerate32)."""
+        fn, name = self._stage_fn("lgf_accelerate", precision)
         p, dev_in, keep = _in_ptr(D, (self.V, 3, 3))
         out, q, dev = _out(None, (self.V, 3, 3), keep.device if dev_in else None)
-        _check(self._lib.lgf_accelerate(self._h, p, q, dev), "lgf_accelerate")
+        _check(fn(self._h, p, q, dev), name)
         del keep
         return out
 
-    def build_g(self, Dt, alpha: float):
+    def build_g(self, Dt, alpha: float, precision: int = 64):
+        """g = reunit(1 + alpha/2 Dt); precision 32: with the FP32 phase's kernels (lgf_build_g32)."""
+        fn, name = self._stage_fn("lgf_build_g", precision)
         p, dev_in, keep = _in_ptr(Dt, (self.V, 3, 3))
         out, q, dev = _out(None, (self.V, 3, 3), keep.device if dev_in else None)
-        _check(self._lib.lgf_build_g(self._h, p, float(alpha), q, dev), "lgf_build_g")
+        _check(fn(self._h, p, float(alpha), q, dev), name)
         del keep
         return out
+
+    def _stage_fn(self, base: str, precision: int):
+        if precision not in (64, 32):
+            raise ValueError("precision must be 64 or 32")
+        name = base if precision == 64 else base + "32"
+        return getattr(self._lib, name), name
 
 
 def lgf_accelerate_noalloc(dims, Delta_in, Dt_out, stream=None) -> None:
