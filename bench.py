@@ -538,12 +538,14 @@ def run_ours(args, dims):
         lw.close()
 
     # end to end through the C ABI from pinned host memory, copies included: every
-    # step copies its input in (lgf_set_links from pinned host memory), fixes it
-    # and reads the fixed links back (lgf_get_links to pinned host memory).  The
-    # steps are dealt alternately to two contexts on two streams, each driven by
-    # its own host thread (the library's calls release the GIL), so that the
-    # copies of one configuration overlap the fix of another; the same steps run
-    # one after another on one context give `serial_value`.
+    # step copies its input in, fixes it and reads the fixed links back
+    # (lgf_get_links to pinned host memory).  The steps alternate between two
+    # contexts on two streams, each driven by its own host thread (the library's
+    # calls release the GIL); the fixes run one at a time in step order, and a
+    # step's copies in (the copy engine into a device buffer, then lgf_set_links)
+    # and out overlap the fixes of its neighbours.  The same steps one after
+    # another on one context, lgf_set_links reading the pinned input in place,
+    # give `serial_value`.
     e2e = None
     if not args.no_e2e:
         import threading
@@ -553,30 +555,51 @@ def run_ours(args, dims):
         nbytes = pin_in[0].numel() * 16
         cdev = torch.cuda.current_device()
 
-        def e2e_step(c, k, out):
-            c.set_links(pin_in[k % len(pin_in)])
-            it = c.fix(args.alpha, args.tol, args.max_iter)["iters"]
+        def copy_out(c, out):
             lgf._check(c._lib.lgf_get_links(c._h, lgf.ctypes.c_void_p(out.data_ptr()), 0), "lgf_get_links")
-            return it
 
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        n_ser = sum(e2e_step(lat, k, pin_out[0]) for k in range(args.steps))
+        n_ser = 0
+        for k in range(args.steps):
+            lat.set_links(pin_in[k % len(pin_in)])
+            n_ser += lat.fix(args.alpha, args.tol, args.max_iter)["iters"]
+            copy_out(lat, pin_out[0])
         torch.cuda.synchronize()
         Ts = time.perf_counter() - t0
         lat2 = lgf.Lattice(dims, stream=torch.cuda.Stream())
         lat2.set_links(dev[1])
         lat2.autotune()
-        e2e_step(lat2, 0, pin_out[1])  # its graph is built here, outside the timed region
+        lat2.fix(args.alpha, args.tol, args.max_iter)  # its graph is built here, outside the timed region
         counts, errs = [0, 0], []
+        turn = [0]
+        cv = threading.Condition()
+        # device landing buffers of the copies in: the copy engine moves the input
+        # while the other context's fix runs, then lgf_set_links packs it on the GPU
+        land = [torch.empty((4, V, 3, 3), dtype=torch.complex128, device="cuda") for _ in range(2)]
 
         def e2e_worker(i, c):
             try:
                 torch.cuda.set_device(cdev)
                 for k in range(i, args.steps, 2):
-                    counts[i] += e2e_step(c, k, pin_out[i])
+                    # during the previous step's fix: H2D copy on this context's stream, then the pack
+                    with torch.cuda.stream(c._stream):
+                        land[i].copy_(pin_in[k % len(pin_in)], non_blocking=True)
+                    c.set_links(land[i])
+                    with cv:
+                        if not cv.wait_for(lambda: turn[0] == k or errs, timeout=600) or errs:
+                            return
+                    try:
+                        counts[i] += c.fix(args.alpha, args.tol, args.max_iter)["iters"]
+                    finally:
+                        with cv:
+                            turn[0] += 1
+                            cv.notify_all()
+                    copy_out(c, pin_out[i])  # during the next step's fix
             except BaseException as e:  # re-raised on the main thread
-                errs.append(e)
+                with cv:
+                    errs.append(e)
+                    cv.notify_all()
 
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -590,6 +613,8 @@ def run_ours(args, dims):
         lat2.close()
         if errs:
             raise errs[0]
+        if turn[0] != args.steps:
+            raise RuntimeError("end-to-end leg: %d of %d steps ran" % (turn[0], args.steps))
         n_e2e = sum(counts)
         Te, n_e2e = reduce_over_ranks(pg, Te, n_e2e)
         Ts, n_ser = reduce_over_ranks(pg, Ts, n_ser)

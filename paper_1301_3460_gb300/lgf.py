@@ -181,6 +181,7 @@ class Lattice:
         self._h = h
         self._lib = lib
         self.mixed = mixed
+        self._stream = None
         if stream is not None:
             self.set_stream(stream)
 
