@@ -26,3 +26,22 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def bench_lattice():
+    """The benchmark lattice: 32^4, eps = 0.3, seed 3202."""
+    from paper_1301_3460_gb300 import inputs
+
+    L = (32, 32, 32, 32)
+    return L, inputs.rough_gauge_field(L, 0.3, 3202)
+
+
+@pytest.fixture(scope="session")
+def bench_lattice_fixed(bench_lattice):
+    """The oracle's whole fix of the benchmark lattice (alpha = 0.08, theta < 1e-15),
+    shared by the full-size FP64 and mixed-precision tests."""
+    from oracle import oracle as orc
+
+    L, U = bench_lattice
+    return orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=500, history=True)

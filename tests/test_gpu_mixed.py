@@ -38,6 +38,28 @@ def test_mixed_matches_fp64_oracle(L, seed):
     assert hist[r["iters_fp32"] - 1, 0] >= 1e-6
 
 
+def test_mixed_benchmark_lattice_against_oracle(bench_lattice, bench_lattice_fixed):
+    """32^4 benchmark lattice in mixed precision (FP32 until theta < 1e-6) against
+    the oracle's FP64 fix: theta < 1e-15, F to 1e-12 relative, links exactly on the
+    input's gauge orbit; their distance to the FP64 links is the residual global
+    rotation left by the FP32 phase (reading 12), a few 1e-7."""
+    L, U = bench_lattice
+    ref = bench_lattice_fixed
+    with lgf.Lattice(L, mixed=True) as lat:
+        lat.set_links(U)
+        r = lat.fix(alpha=0.08, tol=1e-15, max_iter=5000)
+        Um = lat.get_links()
+        G = lat.get_gauge()
+    assert ref["converged"] and r["converged"] and r["theta"] < 1e-15
+    assert r["iters_fp32"] > 0 and r["iters_fp64"] > 0
+    assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
+    assert np.max(np.abs(orc.gauge_transform(L, U, G) - Um)) < 1e-12
+    err = float(np.max(np.abs(Um - ref["U"])))
+    print("32^4 mixed: %d + %d iters vs oracle %d; max|U_mixed - U_oracle| = %.2e" % (
+        r["iters_fp32"], r["iters_fp64"], ref["iters"], err))
+    assert err < 1e-4
+
+
 def test_mixed_full_size_against_fp64_gpu():
     """48^4 (radix-3 FFT lengths): the mixed result against the FP64 GPU path."""
     L = (48, 48, 48, 48)

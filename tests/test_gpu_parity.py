@@ -179,13 +179,6 @@ def test_full_size_one_step():
     assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
 
 
-@pytest.fixture(scope="module")
-def bench_lattice():
-    """The benchmark lattice: 32^4, eps = 0.3, seed 3202."""
-    L = (32, 32, 32, 32)
-    return L, inputs.rough_gauge_field(L, 0.3, 3202)
-
-
 def test_full_size_ten_steps(bench_lattice):
     """32^4 benchmark lattice: links and G after 10 steps against the oracle (1e-13)."""
     L, U = bench_lattice
@@ -199,12 +192,12 @@ def test_full_size_ten_steps(bench_lattice):
     assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
 
 
-def test_full_size_converges_like_oracle(bench_lattice):
+def test_full_size_converges_like_oracle(bench_lattice, bench_lattice_fixed):
     """32^4 benchmark lattice run to theta < 1e-15 in both: the iteration count
     (one apart only when theta_n is within 1e-10 of tol), F to 1e-12 relative,
     links to 1e-11, and the GPU's G relating its links to the input."""
     L, U = bench_lattice
-    ref = orc.fix(L, U, alpha=0.08, tol=1e-15, max_iter=500, history=True)
+    ref = bench_lattice_fixed
     with lgf.Lattice(L) as lat:
         lat.set_links(U)
         r = lat.fix(alpha=0.08, tol=1e-15, max_iter=500)
