@@ -349,6 +349,57 @@ int lgf_gluon_pmin_bwd(lgf_ctx* ctx, double gD, double* gU);
 int lgf_accelerate_noalloc(const int dims[4], const double* Delta_in, double* Dt_out, void* cuda_stream);
 
 /*
+ * One lattice over several ranks (FP64): the counterpart of the paper's MPI
+ * code, whose 4D FFT is distributed by transposes (description of the CPU
+ * implementation).  Rank `rank` of `nranks` holds the t-slab t in [rank nt,
+ * (rank+1) nt), nt = Lt/nranks, every array in the library's site order of an
+ * Lx x Ly x Lz x nt lattice.  The library computes; the caller moves data between
+ * ranks (NCCL, or copies between slabs of one process), through device buffers
+ * of the slab (lgf_slab_buffer, all complex128):
+ *   LGF_SLAB_A, LGF_SLAB_B  the four packed fields of the slab (4 V_slab
+ *       values each) in all-to-all order: A is [j][4][nt][nz][Lx Ly], block j =
+ *       the z-range [j nz, (j+1) nz) of this slab (nz = Lz/nranks); B is
+ *       [i][4][nt][nz][Lx Ly], block i = rank i's t-range of this rank's z-range.
+ *   LGF_SLAB_AH_SEND/RECV  [4][Lz Lx Ly]: the packed anti-Hermitian parts of the
+ *       t-links of a slab's last plane, which enter the next slab's first plane.
+ *   LGF_SLAB_G_SEND/RECV   [9][Lz Lx Ly]: g on a slab's first plane, which is
+ *       g(x + t) of the previous slab's last plane.
+ * One iteration, on every rank in this order (each call on the slab's stream):
+ *   lgf_slab_pack_halo(AH_SEND); send it to rank+1's AH_RECV;
+ *   lgf_slab_delta -> this slab's theta and F (normalised by the slab's sites;
+ *     the lattice's are their means over ranks); stop here if theta < tol;
+ *   all-to-all A -> B (block j of A to rank j, into block `rank` of its B);
+ *   lgf_slab_accelerate; all-to-all B -> A (block i of B to rank i);
+ *   lgf_slab_build_g(alpha); lgf_slab_pack_halo(G_SEND); send it to rank-1's G_RECV;
+ *   lgf_slab_update.
+ * Extents as for lgf_create, Lt and Lz multiples of nranks
+ * (LGF_ERR_UNSUPPORTED_DIMS otherwise).  Links in and out are device pointers
+ * to [4][V_slab][3][3] complex128 (the slab's sites), G to [V_slab][3][3];
+ * lgf_slab_set_links checks SU(3) as lgf_set_links does and sets G = 1.
+ * lgf_slab_delta blocks until its theta and F are known; the other calls return
+ * with their work queued.  Calls before lgf_slab_set_links: LGF_ERR_STATE.
+ */
+typedef struct lgf_slab lgf_slab;
+#define LGF_SLAB_A 0
+#define LGF_SLAB_B 1
+#define LGF_SLAB_AH_SEND 2
+#define LGF_SLAB_AH_RECV 3
+#define LGF_SLAB_G_SEND 4
+#define LGF_SLAB_G_RECV 5
+int lgf_slab_create(const int dims[4], int nranks, int rank, lgf_slab** out);
+void lgf_slab_destroy(lgf_slab* slab);
+int lgf_slab_set_stream(lgf_slab* slab, void* cuda_stream);
+int lgf_slab_set_links(lgf_slab* slab, const double* U);
+int lgf_slab_get_links(lgf_slab* slab, double* U_out);
+int lgf_slab_get_gauge(lgf_slab* slab, double* G_out);
+int lgf_slab_buffer(lgf_slab* slab, int which, void** ptr, size_t* bytes);
+int lgf_slab_pack_halo(lgf_slab* slab, int which);
+int lgf_slab_delta(lgf_slab* slab, double* theta, double* F);
+int lgf_slab_accelerate(lgf_slab* slab);
+int lgf_slab_build_g(lgf_slab* slab, double alpha);
+int lgf_slab_update(lgf_slab* slab);
+
+/*
  * Configurations to fix, made on the device (the paper fixes Wilson-action
  * configurations and does not say how it made them).  These calls change the
  * links stored in ctx in place, in FP64, and reset G to 1.

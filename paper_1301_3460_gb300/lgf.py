@@ -28,6 +28,7 @@ LGF_ERR_NOT_CONVERGED = 5
 LGF_ERR_NAN = 6
 LGF_ERR_TIMEOUT = 7
 LGF_ERR_STATE = 8
+LGF_SLAB_A, LGF_SLAB_B, LGF_SLAB_AH_SEND, LGF_SLAB_AH_RECV, LGF_SLAB_G_SEND, LGF_SLAB_G_RECV = range(6)
 
 LGF_FP64 = 0
 LGF_MIXED = 1
@@ -115,6 +116,18 @@ def load(build_if_missing: bool = True):
             "lgf_batch_get_stats": ([P, I, IP, IP], I),
             "lgf_batch_destroy": ([P], None),
             "lgf_destroy": ([P], None),
+            "lgf_slab_create": ([ctypes.POINTER(ctypes.c_int), I, I, ctypes.POINTER(P)], I),
+            "lgf_slab_destroy": ([P], None),
+            "lgf_slab_set_stream": ([P, P], I),
+            "lgf_slab_set_links": ([P, P], I),
+            "lgf_slab_get_links": ([P, P], I),
+            "lgf_slab_get_gauge": ([P, P], I),
+            "lgf_slab_buffer": ([P, I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_size_t)], I),
+            "lgf_slab_pack_halo": ([P, I], I),
+            "lgf_slab_delta": ([P, DP, DP], I),
+            "lgf_slab_accelerate": ([P], I),
+            "lgf_slab_build_g": ([P, D], I),
+            "lgf_slab_update": ([P], I),
             "lgf_strerror": ([I], ctypes.c_char_p),
             "lgf_last_error": ([], ctypes.c_char_p),
         }

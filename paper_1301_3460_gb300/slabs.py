@@ -102,3 +102,250 @@ class TSlabs:
         else:
             dist.all_to_all_single(recv, send, group=group)
         return recv.permute(1, 2, 0, 3, 4, 5).reshape(C, nt, Lz, Ly, Lx)
+
+
+# ---------------------------------------------------------------- GPU ranks
+
+class _DeviceBuffer:
+    """A library-owned device buffer seen as a flat float64 array (pairs of re, im)."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes // 8,), "typestr": "<f8", "data": (ptr, False),
+                                         "version": 3}
+
+
+class Slab:
+    """One rank's t-slab on the current GPU (the library's lgf_slab_* entry
+    points).  Links and G are complex128 CUDA tensors of the slab's sites,
+    [4, V_slab, 3, 3] and [V_slab, 3, 3]."""
+
+    def __init__(self, dims, nranks: int, rank: int, stream=None):
+        import ctypes
+
+        from . import lgf
+
+        self._lgf = lgf
+        self._lib = lib = lgf.load()
+        self.dims = tuple(int(v) for v in dims)
+        self.nranks, self.rank = int(nranks), int(rank)
+        arr = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        lgf._check(lib.lgf_slab_create(arr, self.nranks, self.rank, ctypes.byref(h)), "lgf_slab_create")
+        self._h = h
+        self.layout = TSlabs(self.dims, self.nranks)
+        Lx, Ly, Lz, _ = self.dims
+        self.V = Lx * Ly * Lz * self.layout.nt
+        self._stream = stream
+        if stream is not None:
+            raw = getattr(stream, "cuda_stream", stream)
+            lgf._check(lib.lgf_slab_set_stream(h, ctypes.c_void_p(raw or 0)), "lgf_slab_set_stream")
+        self._bufs = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._bufs.clear()
+            self._lib.lgf_slab_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _call(self, name, *args):
+        self._lgf._check(getattr(self._lib, name)(self._h, *args), name)
+
+    def buffer(self, which: int):
+        """Flat complex128 tensor over the slab's buffer `which` (LGF_SLAB_*);
+        valid while the slab lives."""
+        import ctypes
+
+        import torch
+
+        if which not in self._bufs:
+            p, n = ctypes.c_void_p(), ctypes.c_size_t()
+            self._call("lgf_slab_buffer", int(which), ctypes.byref(p), ctypes.byref(n))
+            flat = torch.as_tensor(_DeviceBuffer(p.value, n.value), device="cuda")
+            self._bufs[which] = torch.view_as_complex(flat.view(-1, 2))
+        return self._bufs[which]
+
+    def set_links(self, U):
+        import ctypes
+
+        import torch
+
+        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == torch.complex128
+                and tuple(U.shape) == (4, self.V, 3, 3)):
+            raise TypeError("set_links takes a complex128 CUDA tensor (4, %d, 3, 3)" % self.V)
+        U = U.contiguous()
+        self._call("lgf_slab_set_links", ctypes.c_void_p(U.data_ptr()))
+
+    def get_links(self):
+        import ctypes
+
+        import torch
+
+        out = torch.empty((4, self.V, 3, 3), dtype=torch.complex128, device="cuda")
+        self._call("lgf_slab_get_links", ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def get_gauge(self):
+        import ctypes
+
+        import torch
+
+        out = torch.empty((self.V, 3, 3), dtype=torch.complex128, device="cuda")
+        self._call("lgf_slab_get_gauge", ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def pack_halo(self, which: int):
+        self._call("lgf_slab_pack_halo", int(which))
+
+    def delta(self):
+        import ctypes
+
+        th, F = ctypes.c_double(), ctypes.c_double()
+        self._call("lgf_slab_delta", ctypes.byref(th), ctypes.byref(F))
+        return th.value, F.value
+
+    def accelerate(self):
+        self._call("lgf_slab_accelerate")
+
+    def build_g(self, alpha: float):
+        import ctypes
+
+        self._call("lgf_slab_build_g", ctypes.c_double(float(alpha)))
+
+    def update(self):
+        self._call("lgf_slab_update")
+
+
+class LocalExchange:
+    """The exchanges of ranks held as several slabs of one process (one GPU):
+    device copies in place of the messages."""
+
+    def __init__(self, slabs):
+        self.slabs = list(slabs)
+        self.N = len(self.slabs)
+
+    def halo_ah(self):  # a slab's last plane goes up
+        from .lgf import LGF_SLAB_AH_RECV, LGF_SLAB_AH_SEND
+
+        for r, s in enumerate(self.slabs):
+            self.slabs[(r + 1) % self.N].buffer(LGF_SLAB_AH_RECV).copy_(s.buffer(LGF_SLAB_AH_SEND))
+
+    def halo_g(self):  # a slab's first plane goes down
+        from .lgf import LGF_SLAB_G_RECV, LGF_SLAB_G_SEND
+
+        for r, s in enumerate(self.slabs):
+            self.slabs[(r - 1) % self.N].buffer(LGF_SLAB_G_RECV).copy_(s.buffer(LGF_SLAB_G_SEND))
+
+    def all_to_all(self, src: int, dst: int):  # block i of rank r's src -> block r of rank i's dst
+        for r in range(self.N):
+            out = self.slabs[r].buffer(dst).view(self.N, -1)
+            for i in range(self.N):
+                out[i].copy_(self.slabs[i].buffer(src).view(self.N, -1)[r])
+
+    def mean(self, values):
+        n = len(values)
+        return tuple(sum(v[k] for v in values) / n for k in range(len(values[0])))
+
+
+class DistExchange:
+    """The exchanges of one slab per process over a torch.distributed group:
+    NCCL on device buffers, or (staged=True, for gloo) through host copies."""
+
+    def __init__(self, slab: Slab, group=None, staged: bool = False):
+        import torch.distributed as dist
+
+        self.slabs = [slab]
+        self.group = group
+        self.staged = staged
+        self.N = dist.get_world_size(group)
+        self.rank = dist.get_rank(group)
+
+    def _t(self, x):  # what goes on the wire: real views, on the host if staged
+        import torch
+
+        x = torch.view_as_real(x)
+        return x.cpu() if self.staged else x
+
+    def _sendrecv(self, send, recv, to, frm, tag):
+        import torch
+        import torch.distributed as dist
+
+        if self.N == 1:
+            recv.copy_(send)
+            return
+        s, r = self._t(send), (torch.empty_like(self._t(recv)))
+        reqs = dist.batch_isend_irecv([dist.P2POp(dist.isend, s, to, self.group, tag=tag),
+                                       dist.P2POp(dist.irecv, r, frm, self.group, tag=tag)])
+        for q in reqs:
+            q.wait()
+        recv.copy_(torch.view_as_complex(r.to(recv.device)))
+
+    def halo_ah(self):
+        from .lgf import LGF_SLAB_AH_RECV, LGF_SLAB_AH_SEND
+
+        s = self.slabs[0]
+        self._sendrecv(s.buffer(LGF_SLAB_AH_SEND), s.buffer(LGF_SLAB_AH_RECV), (self.rank + 1) % self.N,
+                       (self.rank - 1) % self.N, 1)
+
+    def halo_g(self):
+        from .lgf import LGF_SLAB_G_RECV, LGF_SLAB_G_SEND
+
+        s = self.slabs[0]
+        self._sendrecv(s.buffer(LGF_SLAB_G_SEND), s.buffer(LGF_SLAB_G_RECV), (self.rank - 1) % self.N,
+                       (self.rank + 1) % self.N, 2)
+
+    def all_to_all(self, src: int, dst: int):
+        import torch
+        import torch.distributed as dist
+
+        s = self.slabs[0]
+        a, b = s.buffer(src), s.buffer(dst)
+        if self.N == 1:
+            b.copy_(a)
+            return
+        sa = self._t(a)
+        rb = torch.empty_like(sa)
+        dist.all_to_all_single(rb, sa, group=self.group)
+        b.copy_(torch.view_as_complex(rb.to(b.device)))
+
+    def mean(self, values):
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor(values[0], dtype=torch.float64, device="cpu" if self.staged else "cuda")
+        dist.all_reduce(t, group=self.group)
+        return tuple(float(v) / self.N for v in t.tolist())
+
+
+def fix_slabs(exchange, alpha: float = 0.08, tol: float = 1e-15, max_iter: int = 100000) -> dict:
+    """The Fourier-accelerated iteration of one lattice over the slabs of
+    `exchange` (LocalExchange: all ranks in this process; DistExchange: this
+    process's rank), stopping when theta of the current links is below tol or
+    after max_iter updates, like lgf_fix."""
+    from .lgf import LGF_SLAB_A, LGF_SLAB_AH_SEND, LGF_SLAB_B, LGF_SLAB_G_SEND
+
+    slabs = exchange.slabs
+    n = 0
+    while True:
+        for s in slabs:
+            s.pack_halo(LGF_SLAB_AH_SEND)
+        exchange.halo_ah()
+        theta, F = exchange.mean([s.delta() for s in slabs])
+        if not (theta == theta):
+            raise FloatingPointError("theta is NaN after %d updates" % n)
+        if theta < tol or n >= max_iter:
+            break
+        exchange.all_to_all(LGF_SLAB_A, LGF_SLAB_B)
+        for s in slabs:
+            s.accelerate()
+        exchange.all_to_all(LGF_SLAB_B, LGF_SLAB_A)
+        for s in slabs:
+            s.build_g(alpha)
+            s.pack_halo(LGF_SLAB_G_SEND)
+        exchange.halo_g()
+        for s in slabs:
+            s.update()
+        n += 1
+    return dict(iters=n, theta=theta, F=F, converged=theta < tol)
