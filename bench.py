@@ -62,7 +62,12 @@ def parse():
     ap.add_argument("--no-cpu-fix", action="store_true", help="skip the oracle's full-size fix in cpu_baseline")
     ap.add_argument("--no-48", action="store_true", help="skip the 48^4 FP64-vs-mixed leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 58-lattice ensemble leg")
-    ap.add_argument("--workload", default="single", choices=["single", "ensemble", "wilson", "kernels", "probe"],
+    ap.add_argument("--no-slabs", action="store_true", help="skip the one-GPU measurement of the t-slab path")
+    ap.add_argument("--slab-ranks", type=int, default=2,
+                    help="--workload slabs in one process: t-slabs emulated on one GPU")
+    ap.add_argument("--slab-iters", type=int, default=10, help="iterations per step of --workload slabs")
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "ensemble", "wilson", "kernels", "probe", "slabs"],
                     help="single: the 32^4 lattice line; ensemble: the batched mixed-precision ensemble; "
                          "wilson: Wilson-action configuration generation (heat bath + overrelaxation); "
                          "kernels: the iteration kernels launched one by one (FP64 and FP32), per-kernel times; "
@@ -621,6 +626,13 @@ def run_ours(args, dims):
         e2e = {"value": n_e2e / Te, "unit": "iters/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "contexts": 2, "serial_value": n_ser / Ts}
 
+    # the t-slab decomposition of one lattice (the multi-GPU path) on this GPU: its
+    # own kernels and host-driven exchanges, ranks emulated as slabs of one process
+    slabs = None
+    if not args.no_slabs and pg is None:
+        slabs = {"iterations": 10, "ranks": "emulated on one GPU (device copies in place of messages)",
+                 "iters_per_s": {str(R): slab_rate(dims, host[1], R, 10) for R in (1, 2)}}
+
     # 48^4 (radix-3 FFT lengths): FP64 against mixed precision on one configuration
     big48 = None
     if not args.no_48 and not args.no_mixed:
@@ -714,6 +726,7 @@ def run_ours(args, dims):
             "time_to_theta": ttt, "mixed": mixed, "links18": links18, "links8": links8, "diff": diff,
             "plain_sd_16x4": plain,
             "wilson_generation": wilson, "fix_48x4": big48, "ensemble": ens,
+            "slabs": slabs,
             "roofline": roof, "kernels": kernels, "hbm_iteration": hbm_iter, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
@@ -1023,6 +1036,99 @@ def run_kernels(args, dims):
     return 0
 
 
+def slab_rate(dims, U, nranks: int, n_iter: int, warm: int = 2) -> float:
+    """Iterations per second of the t-slab path with `nranks` slabs emulated on
+    this GPU (device copies in place of the messages), over n_iter iterations
+    from the input links U (host [4, V, 3, 3])."""
+    import torch
+
+    from paper_1301_3460_gb300.slabs import LocalExchange, Slab, fix_slabs
+
+    slabs = [Slab(dims, nranks, r) for r in range(nranks)]
+    try:
+        Vs = U.shape[1] // nranks
+        parts = [torch.from_numpy(np.ascontiguousarray(U[:, r * Vs:(r + 1) * Vs])).cuda() for r in range(nranks)]
+        ex = LocalExchange(slabs)
+        for s, u in zip(slabs, parts):
+            s.set_links(u)
+        fix_slabs(ex, tol=0.0, max_iter=warm)
+        for s, u in zip(slabs, parts):
+            s.set_links(u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fix_slabs(ex, tol=0.0, max_iter=n_iter)
+        torch.cuda.synchronize()
+        T = time.perf_counter() - t0
+    finally:
+        for s in slabs:
+            s.close()
+    return r["iters"] / T
+
+
+def run_slabs(args, dims):
+    """One lattice split into t-slabs: under torchrun one slab per GPU over NCCL
+    (strong scaling: the lattice is fixed), else --slab-ranks slabs emulated on
+    one GPU.  A step is --slab-iters iterations from the eps = 0.3 configuration;
+    the host drives the loop (one theta/F reduction and four exchanges per
+    iteration)."""
+    import torch
+
+    from paper_1301_3460_gb300 import inputs
+    from paper_1301_3460_gb300.slabs import DistExchange, LocalExchange, Slab, fix_slabs
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    U = inputs.rough_gauge_field(dims, EPS[1], SEEDS[1])
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        N = ws
+        slabs = [Slab(dims, N, rank, stream=torch.cuda.current_stream())]
+        ex = DistExchange(slabs[0])
+        mine = [rank]
+    else:
+        N = args.slab_ranks
+        slabs = [Slab(dims, N, r) for r in range(N)]
+        ex = LocalExchange(slabs)
+        mine = list(range(N))
+    Vs = U.shape[1] // N
+    parts = {r: torch.from_numpy(np.ascontiguousarray(U[:, r * Vs:(r + 1) * Vs])).cuda() for r in mine}
+
+    def step():
+        for s, r in zip(slabs, mine):
+            s.set_links(parts[r])
+        return fix_slabs(ex, tol=0.0, max_iter=args.slab_iters)["iters"]
+
+    for _ in range(args.warmup):
+        step()
+    if ws > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = sum(step() for _ in range(args.steps))
+    torch.cuda.synchronize()
+    T = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([T], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        T = float(t.item())
+    for s in slabs:
+        s.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "SD iters/s of one %s lattice split into %d t-slabs" % ("x".join(map(str, dims)), N),
+            "value": n / T, "unit": "iters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * T / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "t-slab decomposition, FP64, eps 0.3, %d iterations per step" % args.slab_iters,
+                       "dims": list(dims), "slabs": N,
+                       "ranks": "one per GPU over NCCL" if ws > 1 else "emulated on one GPU"}}), flush=True)
+    if ws > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
 def run_probe(args):
     """FP64 and FP32 FMA rates (best of --steps launches after --warmup), with the
     SM clock sampled during the launches."""
@@ -1059,6 +1165,8 @@ def main():
     if args.workload == "wilson":
         dims = tuple(int(v) for v in args.dims.split(","))
         return run_wilson(args, dims)
+    if args.workload == "slabs":
+        return run_slabs(args, tuple(int(v) for v in args.dims.split(",")))
     dims = tuple(int(v) for v in args.dims.split(","))
     if args.impl == "reference":
         return run_reference(args, dims)
