@@ -52,7 +52,8 @@ typedef enum {
     LGF_ERR_UNSUPPORTED_DIMS = 4, /* an extent or the plane sizes are outside what the FFT kernels take */
     LGF_ERR_NOT_CONVERGED = 5,    /* max_iter updates applied before theta < tol */
     LGF_ERR_NAN = 6,              /* theta or F became NaN or infinite */
-    LGF_ERR_TIMEOUT = 7,          /* the device loop hit its safety bound on body executions */
+    LGF_ERR_TIMEOUT = 7,          /* the device loop hit its safety bound on body executions, or a
+                                     kernel gave up waiting (about a second) for its own tensor copies */
     LGF_ERR_STATE = 8             /* call out of order (e.g. lgf_fix before lgf_set_links) */
 } lgf_status;
 
@@ -190,6 +191,23 @@ int lgf_set_fp32_refresh(lgf_ctx* ctx, int every);
 int lgf_set_fp32_update(lgf_ctx* ctx, int fused);
 
 /*
+ * LGF_MIXED: precision of the accelerator (forward 4D FFT of Delta, the
+ * multiplier p2max/(p2(k) V), inverse FFT; the introduction's Fourier
+ * acceleration) in the FP64 iterations.  64 (default): every step of an FP64
+ * iteration in FP64.  32: Delta, theta, F, the Gram-Schmidt of g and the update
+ * stay in FP64 (the fix still stops on the FP64 theta < theta_tol and keeps the
+ * links on the input's gauge orbit in FP64), while Delta is rounded to FP32 for
+ * the transforms, which run in the FP32 phase's kernels.  The accelerator only
+ * preconditions the step: Delta~ = 0 exactly when Delta = 0, so its rounding
+ * changes how fast theta falls (relative error ~1e-7 per mode), not where the
+ * iteration stops.  With switch_tol above the first theta the FP32 phase is
+ * empty and the whole fix runs in FP64 with the FP32 accelerator.  Needs a
+ * mixed context without LGF_PLAIN_SD (LGF_ERR_STATE otherwise); other values:
+ * LGF_ERR_ARG.  lgf_batch_set_accel_precision sets every lattice of a batch.
+ */
+int lgf_set_accel_precision(lgf_ctx* ctx, int precision);
+
+/*
  * Stage entry points (same arithmetic as inside lgf_fix, exposed for checking
  * each step on its own).  All arrays are caller-owned, layouts as above.
  *
@@ -239,13 +257,34 @@ int lgf_time_kernels(lgf_ctx* ctx, double alpha, int n_iter, int precision, doub
 
 /*
  * lgf_autotune: choose the launch shapes of the shared-memory FFT kernels (block
- * sizes of the plane and pencil kernels, x-columns per z,t pencil) for this lattice by
+ * sizes of the plane and pencil kernels, x-columns per z,t pencil and the z,t
+ * kernel's form, see lgf_set_shape) for this lattice by
  * timing the candidates on the stored links; both precisions of a mixed
  * context.  The choice is cached for the process by extents and precision.
  * Needs lgf_set_links first (LGF_ERR_STATE otherwise).  Changes no result
  * beyond rounding.
  */
 int lgf_autotune(lgf_ctx* ctx);
+
+/*
+ * lgf_set_shape / lgf_get_shape (instrumentation, no counterpart in the paper):
+ * the launch shape of the FFT kernels of one precision (64: the FP64 kernels;
+ * 32: the FP32 phase's, mixed contexts only, LGF_ERR_STATE otherwise).
+ *   nt_xy, nt_zt  threads per block of the xy-plane kernels and of the z,t kernel
+ *                 (multiples of 32; at most 128 in FP64, 256 in FP32)
+ *   xw            x-columns per z,t pencil (a power of two dividing Lx)
+ *   zt_form       0: the pencil-tiled z,t kernel (one block per pencil);
+ *                 1: the persistent z,t kernel whose pencils are staged by tensor
+ *                 copies (TMA) into two shared-memory buffers guarded by
+ *                 mbarriers (FP32: xw >= 2; its grid fills the device)
+ * lgf_set_shape returns LGF_ERR_ARG for a shape the kernels cannot run
+ * (including a form-1 shape whose buffers exceed shared memory); it waits for the
+ * context's stream and replaces the captured loop.  lgf_autotune overwrites it.
+ * lgf_get_shape writes {nt_xy, nt_zt, xw, zt_form, grid of form 1} to shape_out[5].
+ * Every shape gives the same results up to rounding.
+ */
+int lgf_set_shape(lgf_ctx* ctx, int precision, int nt_xy, int nt_zt, int xw, int zt_form);
+int lgf_get_shape(lgf_ctx* ctx, int precision, int* shape_out);
 
 /*
  * lgf_probe_fma (instrumentation, no counterpart in the paper): the FMA rate of
@@ -291,6 +330,7 @@ typedef struct lgf_batch lgf_batch;
 int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out);
 int lgf_batch_set_stream(lgf_batch* b, void* cuda_stream);
 int lgf_batch_set_switch_tol(lgf_batch* b, double switch_tol);  /* every lattice, as lgf_set_switch_tol */
+int lgf_batch_set_accel_precision(lgf_batch* b, int precision);  /* every lattice, as lgf_set_accel_precision */
 int lgf_batch_set_links(lgf_batch* b, int i, const double* U, int on_device);
 int lgf_batch_fix(lgf_batch* b, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta,
                   int* status, double* t_retire_ms);

@@ -94,6 +94,7 @@ struct lgf_ctx {
     float2* AH32 = nullptr;   // FP32 phase without the fused update: packed anti-Hermitian
     float* Fs32 = nullptr;    // parts and Re Tr handed from the update to the Delta kernel
     bool fused32 = false;     // FP32 phase: update fused with Delta (links recomputed) or not
+    bool accel32 = false;     // FP64 iterations take the accelerator's transforms in FP32
     void* Fd = nullptr;       // [4][V] double2 (the FP32 phase uses the front half as float2)
     double2* AH64 = nullptr;  // [4][4][V] packed anti-Hermitian parts of the links
     double* Fs64 = nullptr;   // [V] Re Tr of the four links of a site
@@ -132,16 +133,26 @@ namespace {
 
 // Shared-memory FFT tiles: the four fields of an xy-plane, and one z,t pencil of
 // xw x-columns; thread counts a multiple of 32 up to 128 (FP64) or 256 (FP32).
-bool make_shape(const Lat& d, size_t elem, int nt_xy, int nt_zt, int xw, Shape* sh)
+// zt_form 1: the persistent z,t kernel with TMA-staged pencils (its grid from
+// the device's occupancy, so only with a GPU present).
+bool make_shape(const Lat& d, size_t elem, int nt_xy, int nt_zt, int xw, Shape* sh, int zt_form = 0)
 {
     const int ntmax = elem == sizeof(double2) ? 128 : 256;  // the tile kernels' launch bounds
     if (nt_xy < 32 || nt_xy > ntmax || nt_xy % 32 || nt_zt < 32 || nt_zt > ntmax || nt_zt % 32) return false;
     if (plane_tile_bytes(d, elem) > kTileBudget) return false;
     if (xw < 1 || (xw & (xw - 1)) || d.L[0] % xw) return false;  // a power of two dividing Lx
     if (pencil_tile_bytes(d, xw, elem) > kTileBudget) return false;
+    if (zt_form < 0 || zt_form > 1) return false;
+    int grid = 0;
+    if (zt_form == 1) {
+        grid = elem == sizeof(double2) ? zt_tma_grid<double>(d, nt_zt, xw) : zt_tma_grid<float>(d, nt_zt, xw);
+        if (grid <= 0) return false;
+    }
     sh->nt_xy = nt_xy;
     sh->nt_zt = nt_zt;
     sh->xw = xw;
+    sh->zt_tma = zt_form;
+    sh->zt_grid = grid;
     return true;
 }
 
@@ -164,18 +175,44 @@ template <> const Shape& shape_of<float>(const lgf_ctx* c) { return c->sh32; }
 
 // one FP64 iteration after Delta: FFT(z,t)+scale+IFFT(t,z), IFFT(x,y)+g, update,
 // Delta+FFT(x,y)
+// Delta, theta and F of the FP64 links with the forward x,y transform: in FP64, or
+// in FP32 into the front half of Fd when the accelerator runs in FP32
+void launch_delta64(lgf_ctx* c, cudaStream_t s, Ctl* ctl, double2* hist)
+{
+    if (c->accel32 && !c->plain)
+        launch_delta64_f32(c->lat, c->sh64, s, c->AH64, c->Fs64, reinterpret_cast<float2*>(c->Fd), c->partials, ctl,
+                           hist);
+    else
+        launch_delta<double>(c->lat, c->sh64, c->tb, s, c->AH64, c->Fs64, reinterpret_cast<double2*>(c->Fd),
+                             c->partials, ctl, hist, !c->plain);
+}
+
+// the accelerator and the g builder of an FP64 iteration: FP64 transforms, or FP32
+// transforms (z,t kernel of the FP32 phase, FP32 inverse x,y with the FP64
+// Gram-Schmidt writing the FP64 g)
+void launch_accel_g64(lgf_ctx* c, cudaStream_t s, Ctl* ctl)
+{
+    double2* Fd = reinterpret_cast<double2*>(c->Fd);
+    if (c->accel32) {
+        float2* Fd32 = reinterpret_cast<float2*>(c->Fd);
+        launch_zt<float>(c->lat32, c->sh32, c->tb, s, Fd32, ctl);
+        launch_xyinv_g32_64(c->lat32, c->sh32, s, Fd32, c->g64, ctl);
+    } else {
+        launch_zt<double>(c->lat, c->sh64, c->tb, s, Fd, ctl);
+        launch_xyinv_g<double>(c->lat, c->sh64, c->tb, s, Fd, c->g64, ctl);
+    }
+}
+
 void launch_body64(lgf_ctx* c, cudaStream_t s, double2* G)
 {
     double2* Fd = reinterpret_cast<double2*>(c->Fd);
     const Lat& d = c->lat;
-    if (c->plain) {
+    if (c->plain)
         launch_build_g<double>(d, s, Fd, c->g64, c->ctl);
-    } else {
-        launch_zt<double>(d, c->sh64, c->tb, s, Fd, c->ctl);
-        launch_xyinv_g<double>(d, c->sh64, c->tb, s, Fd, c->g64, c->ctl);
-    }
+    else
+        launch_accel_g64(c, s, c->ctl);
     launch_update<double>(d, s, c->U64, G, c->g64, c->ctl, c->AH64, c->Fs64);
-    launch_delta<double>(d, c->sh64, c->tb, s, c->AH64, c->Fs64, Fd, c->partials, c->ctl, c->hist, !c->plain);
+    launch_delta64(c, s, c->ctl, c->hist);
 }
 
 // one FP32-phase iteration after Delta: FFT(z,t)+scale+IFFT(t,z), IFFT(x,y)+g, then
@@ -296,7 +333,6 @@ int add_loop32(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps
 // receives the terminal node.
 int append_fix(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps)
 {
-    double2* Fd64 = reinterpret_cast<double2*>(c->Fd);
     if (c->mixed) {
         CKR(capture_begin(c, graph, deps));
         launch_mixed_prep(c->cap, c->V, c->lat.ne, c->U64, c->U32, c->G32, c->ctl);
@@ -306,15 +342,13 @@ int append_fix(lgf_ctx* c, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps
         CKR(capture_begin(c, graph, deps));
         launch_switch(c->cap, c->lat, c->G32, c->g64, c->U64, c->G64, c->ctl);
         launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
-        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
-                             !c->plain);
+        launch_delta64(c, c->cap, c->ctl, c->hist);
         CKR(capture_end(c, deps));
         CKR(add_loop64(c, graph, deps, c->G64));
     } else {
         CKR(capture_begin(c, graph, deps));
         launch_ah_init<double>(c->lat, c->cap, c->U64, c->AH64, c->Fs64);
-        launch_delta<double>(c->lat, c->sh64, c->tb, c->cap, c->AH64, c->Fs64, Fd64, c->partials, c->ctl, c->hist,
-                             !c->plain);
+        launch_delta64(c, c->cap, c->ctl, c->hist);
         CKR(capture_end(c, deps));
         CKR(add_loop64(c, graph, deps, c->track ? c->G64 : nullptr));
     }
@@ -570,6 +604,19 @@ int reset_stage_ctl(lgf_ctx* c, double alpha = 0.0)
     return LGF_OK;
 }
 
+// LGF_ERR_TIMEOUT when a kernel of the last stage call gave up waiting for its own
+// tensor copies (Ctl::fault of the stage state)
+int stage_fault(lgf_ctx* c)
+{
+    CK(cudaMemcpyAsync(&c->host_ctl->fault, &c->ctl_stage->fault, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->host_ctl->fault) {
+        set_error("a z,t kernel gave up waiting for its tensor copies", cudaSuccess, __FILE__, __LINE__);
+        return LGF_ERR_TIMEOUT;
+    }
+    return LGF_OK;
+}
+
 // ---------------------------------------------------------------- autotuner
 
 // Launch shapes of the plane-tiled kernels are chosen per lattice shape and
@@ -653,18 +700,21 @@ template <typename T> int autotune_prec(lgf_ctx* c)
             best.nt_xy = cand.nt_xy;
         }
     }
-    for (int nt : nts)
-        for (int xw = 1; xw <= 16; xw <<= 1) {
-            Shape cand;
-            if (!make_shape(lat_of<T>(c), elem, best.nt_xy, nt, xw, &cand)) continue;
-            float ms;
-            CKR(time_shape<T>(c, cand, 1, &ms));
-            if (ms < best_zt) {
-                best_zt = ms;
-                best.nt_zt = cand.nt_zt;
-                best.xw = cand.xw;
+    for (int form = 0; form <= 1; form++)
+        for (int nt : nts)
+            for (int xw = 1; xw <= 16; xw <<= 1) {
+                Shape cand;
+                if (!make_shape(lat_of<T>(c), elem, best.nt_xy, nt, xw, &cand, form)) continue;
+                float ms;
+                CKR(time_shape<T>(c, cand, 1, &ms));
+                if (ms < best_zt) {
+                    best_zt = ms;
+                    best.nt_zt = cand.nt_zt;
+                    best.xw = cand.xw;
+                    best.zt_tma = cand.zt_tma;
+                    best.zt_grid = cand.zt_grid;
+                }
             }
-        }
     shape_ref<T>(c) = best;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tuned[key] = best;
@@ -794,6 +844,10 @@ Ctl initial_ctl(const lgf_ctx* c, double alpha, double tol, int max_iter)
 
 int status_of(const Ctl& r)
 {
+    if (r.fault) {
+        set_error("a z,t kernel gave up waiting for its tensor copies", cudaSuccess, __FILE__, __LINE__);
+        return LGF_ERR_TIMEOUT;
+    }
     if (r.nan_seen) return LGF_ERR_NAN;
     if (r.converged) return LGF_OK;
     if (!r.done) return LGF_ERR_TIMEOUT;
@@ -816,7 +870,7 @@ const char* lgf_strerror(int status)
     case LGF_ERR_UNSUPPORTED_DIMS: return "unsupported lattice extents";
     case LGF_ERR_NOT_CONVERGED: return "not converged within max_iter";
     case LGF_ERR_NAN: return "theta or F became NaN or infinite";
-    case LGF_ERR_TIMEOUT: return "device loop hit its safety bound";
+    case LGF_ERR_TIMEOUT: return "device loop hit its safety bound, or a kernel timed out on its own copies";
     case LGF_ERR_STATE: return "call out of order";
     default: return "unknown status";
     }
@@ -877,6 +931,20 @@ int lgf_set_fp32_refresh(lgf_ctx* c, int every)
     if (every != c->refresh_every) {
         c->refresh_every = every;
         drop_graph(c);  // the interval is a launch argument of the captured body
+    }
+    return LGF_OK;
+}
+
+int lgf_set_accel_precision(lgf_ctx* c, int precision)
+{
+    if (!c || (precision != 64 && precision != 32)) return LGF_ERR_ARG;
+    if (!c->mixed || c->plain) return LGF_ERR_STATE;
+    const bool on = precision == 32;
+    if (on) CK(prepare_accel32(c->lat));
+    if (c->accel32 != on) {
+        CK(cudaStreamSynchronize(c->stream));
+        c->accel32 = on;
+        drop_graph(c);
     }
     return LGF_OK;
 }
@@ -1054,7 +1122,8 @@ int lgf_accelerate(lgf_ctx* c, const double* Delta_in, double* Dt_out, int on_de
     CKR(stage_out_begin(c, Dt_out, bytes, on_device, &dst, &copy));
     launch_unpack_delta(c->stream, c->V, Fd, dst);
     CK(cudaGetLastError());
-    return stage_out_end(c, Dt_out, bytes, copy);
+    CKR(stage_out_end(c, Dt_out, bytes, copy));
+    return stage_fault(c);
 }
 
 int lgf_build_g(lgf_ctx* c, const double* Dt_in, double alpha, double* g_out, int on_device)
@@ -1140,7 +1209,8 @@ int lgf_accelerate32(lgf_ctx* c, const double* Delta_in, double* Dt_out, int on_
     CKR(stage_out_begin(c, Dt_out, bytes, on_device, &dst, &copy));
     launch_unpack_delta(c->stream, c->V, c->g64, dst);
     CK(cudaGetLastError());
-    return stage_out_end(c, Dt_out, bytes, copy);
+    CKR(stage_out_end(c, Dt_out, bytes, copy));
+    return stage_fault(c);
 }
 
 int lgf_build_g32(lgf_ctx* c, const double* Dt_in, double alpha, double* g_out, int on_device)
@@ -1190,13 +1260,24 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
     for (int it = 0; it < n_iter && rc == LGF_OK; it++) {
         cudaEventRecord(ev[0], s);
         if (precision == 64) {
+            // the kernels lgf_fix runs (the accelerator in FP32 when so set)
             double2* Fd = reinterpret_cast<double2*>(c->Fd);
-            launch_delta<double>(c->lat, c->sh64, c->tb, s, c->AH64, c->Fs64, Fd, c->partials, c->ctl_stage, nullptr,
-                                 true);
+            float2* Fd32 = reinterpret_cast<float2*>(c->Fd);
+            if (c->accel32)
+                launch_delta64_f32(c->lat, c->sh64, s, c->AH64, c->Fs64, Fd32, c->partials, c->ctl_stage, nullptr);
+            else
+                launch_delta<double>(c->lat, c->sh64, c->tb, s, c->AH64, c->Fs64, Fd, c->partials, c->ctl_stage,
+                                     nullptr, true);
             cudaEventRecord(ev[1], s);
-            launch_zt<double>(c->lat, c->sh64, c->tb, s, Fd, c->ctl_stage);
+            if (c->accel32)
+                launch_zt<float>(c->lat32, c->sh32, c->tb, s, Fd32, c->ctl_stage);
+            else
+                launch_zt<double>(c->lat, c->sh64, c->tb, s, Fd, c->ctl_stage);
             cudaEventRecord(ev[2], s);
-            launch_xyinv_g<double>(c->lat, c->sh64, c->tb, s, Fd, c->g64, c->ctl_stage);
+            if (c->accel32)
+                launch_xyinv_g32_64(c->lat32, c->sh32, s, Fd32, c->g64, c->ctl_stage);
+            else
+                launch_xyinv_g<double>(c->lat, c->sh64, c->tb, s, Fd, c->g64, c->ctl_stage);
             cudaEventRecord(ev[3], s);
             launch_update<double>(c->lat, s, c->U64, c->track ? c->G64 : nullptr, c->g64, c->ctl_stage, c->AH64,
                                   c->Fs64);
@@ -1254,6 +1335,34 @@ int lgf_autotune(lgf_ctx* c)
     return autotune_ctx(c);
 }
 
+int lgf_set_shape(lgf_ctx* c, int precision, int nt_xy, int nt_zt, int xw, int zt_form)
+{
+    if (!c || (precision != 64 && precision != 32)) return LGF_ERR_ARG;
+    if (precision == 32 && !c->mixed) return LGF_ERR_STATE;
+    Shape sh;
+    const bool ok = precision == 64 ? make_shape(c->lat, sizeof(double2), nt_xy, nt_zt, xw, &sh, zt_form)
+                                    : make_shape(c->lat32, sizeof(float2), nt_xy, nt_zt, xw, &sh, zt_form);
+    CK(cudaGetLastError());
+    if (!ok) return LGF_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    (precision == 64 ? c->sh64 : c->sh32) = sh;
+    drop_graph(c);
+    return LGF_OK;
+}
+
+int lgf_get_shape(lgf_ctx* c, int precision, int* shape_out)
+{
+    if (!c || !shape_out || (precision != 64 && precision != 32)) return LGF_ERR_ARG;
+    if (precision == 32 && !c->mixed) return LGF_ERR_STATE;
+    const Shape& sh = precision == 64 ? c->sh64 : c->sh32;
+    shape_out[0] = sh.nt_xy;
+    shape_out[1] = sh.nt_zt;
+    shape_out[2] = sh.xw;
+    shape_out[3] = sh.zt_tma;
+    shape_out[4] = sh.zt_grid;
+    return LGF_OK;
+}
+
 int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out)
 {
     if (n < 1 || !dims || !out) return LGF_ERR_ARG;
@@ -1309,6 +1418,16 @@ int lgf_batch_set_switch_tol(lgf_batch* b, double tol)
 {
     if (!b || !(tol >= 0)) return LGF_ERR_ARG;
     for (lgf_ctx* c : b->ctx) c->switch_tol = tol;
+    return LGF_OK;
+}
+
+int lgf_batch_set_accel_precision(lgf_batch* b, int precision)
+{
+    if (!b) return LGF_ERR_ARG;
+    for (lgf_ctx* c : b->ctx) CKR(lgf_set_accel_precision(c, precision));
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
     return LGF_OK;
 }
 

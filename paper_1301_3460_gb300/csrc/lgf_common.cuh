@@ -259,6 +259,7 @@ struct Ctl {
     int stall;             // FP32 phase ends after this many iterations without a new smallest theta (0: never) ...
     int stall_near;        // ... or after this many once theta_best < near_floor
     double near_floor;
+    int fault;             // a kernel gave up waiting for its own asynchronous copies (loop stopped)
 };
 
 }  // namespace lgf

@@ -14,6 +14,40 @@ namespace {
 inline unsigned blocks(long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 }  // namespace
 
+cudaError_t prepare_accel32(const Lat& d)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    if ((size_t)optin < plane_smem_bytes(d, sizeof(float2)) + 1024) return cudaErrorInvalidValue;
+    if ((e = allow_max_smem(k_delta<double, true, 32, float>, optin))) return e;
+    if ((e = allow_max_smem(k_delta<double, true, 128, float>, optin))) return e;
+    if ((e = allow_max_smem(k_xyinv_g<float, double, 32>, optin))) return e;
+    if ((e = allow_max_smem(k_xyinv_g<float, double, 128>, optin))) return e;
+    return cudaSuccess;
+}
+
+void launch_delta64_f32(const Lat& d, const Shape& sh64, cudaStream_t s, const double2* AH, const double* Fs,
+                        float2* Fd, double* partials, Ctl* ctl, double2* hist)
+{
+    const size_t sm = plane_smem_bytes(d, sizeof(float2));
+    if (small_plane<double>(d))
+        k_delta<double, true, 32, float><<<d.nplanes, sh64.nt_xy, sm, s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+    else
+        k_delta<double, true, 128, float><<<d.nplanes, sh64.nt_xy, sm, s>>>(d, AH, Fs, Fd, partials, ctl, hist);
+}
+
+void launch_xyinv_g32_64(const Lat& d, const Shape& sh32, cudaStream_t s, const float2* Fd, double2* g,
+                         const Ctl* ctl)
+{
+    const size_t sm = plane_smem_bytes(d, sizeof(float2));
+    if (small_plane<float>(d))
+        k_xyinv_g<float, double, 32><<<d.nplanes, sh32.nt_xy, sm, s>>>(d, Fd, g, ctl);
+    else
+        k_xyinv_g<float, double, 128><<<d.nplanes, sh32.nt_xy, sm, s>>>(d, Fd, g, ctl);
+}
+
 void launch_pack_links64(cudaStream_t s, int V, int ne, const double* in, double2* U, unsigned long long* err)
 {
     k_pack_links<double><<<blocks(4L * V, 256), 256, 0, s>>>(V, ne, in, U, err, 1);

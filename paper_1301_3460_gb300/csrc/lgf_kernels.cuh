@@ -91,10 +91,11 @@ __device__ __forceinline__ void block_copy(int n, SRC src, DST dst)
 // out for the forward transform; the reverse for the inverse).  The lanes of a
 // line (pass_lanes(L) of them) work together, so every thread of the block
 // calls this with the same nlines; lines are dealt out a warp at a time.
-template <typename T, int L, bool INV, typename LD, typename ST>
+// NL > 0 sets the lanes per line (default: pass_lanes).
+template <typename T, int L, bool INV, int NL = 0, typename LD, typename ST>
 __device__ __forceinline__ void lines_pass(int nlines, LD ld, ST st)
 {
-    constexpr int Tl = pass_lanes<T>(L), R = L / Tl, W = 32 / Tl;
+    constexpr int Tl = NL > 0 ? NL : pass_lanes<T>(L), R = L / Tl, W = 32 / Tl;
     const int lane = (int)threadIdx.x & 31, tau = lane / W, w = lane - tau * W;
     const int step = ((int)blockDim.x >> 5) * W;
     for (int l0 = ((int)threadIdx.x >> 5) * W; l0 < nlines; l0 += step) {
@@ -369,17 +370,28 @@ __global__ void __launch_bounds__(256) k_ah_init(Lat d, const vec2_t<T>* __restr
     Fs[s] = f;
 }
 
+// Delta rounded to the precision of the transform (TF): FP64 -> FP32 on the
+// integer pipe (d2f_int, round to nearest even)
+template <typename TF> __device__ __forceinline__ cx<TF> to_tf(cx<double> v)
+{
+    if constexpr (sizeof(TF) == 8) return v;
+    else return mk<float>(d2f_int(v.re), d2f_int(v.im));
+}
+
 // One block per xy-plane.  Delta(x) = sum_mu ah_mu(x - mu) - ah_mu(x) (packed
 // fields), theta and F reduced in FP64; with FFT, the forward transform along x
 // (rows of the plane tile) and y (columns, stored straight to Fd), else Delta
-// itself to Fd.  Shared memory: the plane tile (FFT only).
-template <typename T, bool FFT, int LMAX>
+// itself to Fd.  Shared memory: the plane tile (FFT only).  TF: precision of the
+// transform and of Fd (FP64 links with TF = float: Delta, theta and F from the
+// FP64 parts, the transform in FP32).
+template <typename T, bool FFT, int LMAX, typename TF = T>
 __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_delta(Lat d, const vec2_t<T>* __restrict__ AH, const T* __restrict__ Fs,
-                                               vec2_t<T>* __restrict__ Fd, double* __restrict__ partials, Ctl* ctl,
+                                               vec2_t<TF>* __restrict__ Fd, double* __restrict__ partials, Ctl* ctl,
                                                double2* hist)
 {
+    static_assert(sizeof(T) == sizeof(TF) || sizeof(T) == 8, "FP32 links take FP32 transforms");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    vec2_t<TF>* sm = reinterpret_cast<vec2_t<TF>*>(smem_raw);
     if (ld_flag(&ctl->phase_done)) return;
     const int P = d.P, V = d.V, Lx = d.L[0];
     const int plane = blockIdx.x;
@@ -465,19 +477,19 @@ __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k
         th += (double)theta_site(D);
         if (FFT) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) st<T>(sm + k * fs + y * rsx + x, D[k]);
+            for (int k = 0; k < 4; k++) st<TF>(sm + k * fs + y * rsx + x, to_tf<TF>(D[k]));
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) st<T>(Fd + (size_t)k * V + s, D[k]);
+            for (int k = 0; k < 4; k++) st<TF>(Fd + (size_t)k * V + s, to_tf<TF>(D[k]));
         }
     }
     }
     reduce_theta_F(th, fsum, partials, ctl, hist, V);
     if (FFT) {
         __syncthreads();
-        tile_x_lines<T, false, LMAX>(d, sm);
+        tile_x_lines<TF, false, LMAX>(d, sm);
         __syncthreads();
-        plane_y_lines<T, false, LMAX>(d, sm, fs, rsx, Fd + s0, V, Lx);
+        plane_y_lines<TF, false, LMAX>(d, sm, fs, rsx, Fd + s0, V, Lx);
     }
 }
 

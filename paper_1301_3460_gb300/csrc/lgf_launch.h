@@ -22,9 +22,11 @@ struct Tables {
 
 // launch shape of the tiled FFT kernels of one precision
 struct Shape {
-    int nt_xy;   // threads of the xy-plane kernels (a multiple of 32, at most 256)
-    int nt_zt;   // threads of the zt-pencil kernel (likewise)
-    int xw;      // x-columns per zt pencil (divides Lx)
+    int nt_xy = 0;    // threads of the xy-plane kernels (a multiple of 32, at most 256)
+    int nt_zt = 0;    // threads of the zt-pencil kernel (likewise)
+    int xw = 0;       // x-columns per zt pencil (divides Lx)
+    int zt_tma = 0;   // z,t kernel: 0 one block per pencil, 1 persistent with TMA-staged pencils
+    int zt_grid = 0;  // blocks of the persistent form (zt_tma_grid)
 };
 
 // shared memory of the plane tile and of one pencil (element size elem)
@@ -40,6 +42,9 @@ void launch_delta(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t 
 template <typename T> void launch_ah_init(const Lat& d, cudaStream_t s, const vec2_t<T>* U, vec2_t<T>* AH, T* Fs);
 template <typename T>
 void launch_zt(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, vec2_t<T>* Fd, const Ctl* ctl);
+// blocks of the TMA-staged z,t kernel for this lattice, nt threads and pencils
+// of xw columns (0: the form cannot run that shape)
+template <typename T> int zt_tma_grid(const Lat& d, int nt, int xw);
 template <typename T>
 void launch_xyinv_g(const Lat& d, const Shape& sh, const Tables& tb, cudaStream_t s, const vec2_t<T>* Fd,
                     vec2_t<T>* g, const Ctl* ctl);
@@ -57,6 +62,16 @@ void launch_update_delta32(const Lat& d, cudaStream_t s, const float2* Uin, floa
                            Ctl* ctl, float2* Fd, double* partials, double2* hist);
 void launch_delta_links32(const Lat& d, cudaStream_t s, const float2* U, float2* Fd, double* partials, Ctl* ctl,
                           double2* hist, int every);
+
+// FP64 iterations with the accelerator in FP32 (FP64 unit): Delta, theta and F
+// from the FP64 packed parts with the forward x,y transform in FP32 (Fd32), and
+// the FP32 inverse x,y transform with the FP64 Gram-Schmidt writing an FP64 g;
+// the FP32 z,t kernel (launch_zt<float>) sits between them
+cudaError_t prepare_accel32(const Lat& d);
+void launch_delta64_f32(const Lat& d, const Shape& sh64, cudaStream_t s, const double2* AH, const double* Fs,
+                        float2* Fd, double* partials, Ctl* ctl, double2* hist);
+void launch_xyinv_g32_64(const Lat& d, const Shape& sh32, cudaStream_t s, const float2* Fd, double2* g,
+                         const Ctl* ctl);
 
 // conversion, checking and mode-switch kernels (FP64 unit)
 void launch_pack_links64(cudaStream_t s, int V, int ne, const double* in, double2* U, unsigned long long* err);

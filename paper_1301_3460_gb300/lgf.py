@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
             "lgf_set_switch_tol": ([P, D], I),
             "lgf_set_fp32_refresh": ([P, I], I),
             "lgf_set_fp32_update": ([P, I], I),
+            "lgf_set_accel_precision": ([P, I], I),
+            "lgf_batch_set_accel_precision": ([P, I], I),
             "lgf_set_loop_bound": ([P, I], I),
             "lgf_delta": ([P, P, I, DP, DP], I),
             "lgf_accelerate": ([P, P, P, I], I),
@@ -93,6 +95,8 @@ def load(build_if_missing: bool = True):
             "lgf_time_kernels": ([P, D, I, I, DP], I),
             "lgf_accelerate_noalloc": ([ctypes.POINTER(ctypes.c_int), P, P, P], I),
             "lgf_autotune": ([P], I),
+            "lgf_set_shape": ([P, I, I, I, I, I], I),
+            "lgf_get_shape": ([P, I, ctypes.POINTER(ctypes.c_int)], I),
             "lgf_probe_fma": ([I, I, DP, DP], I),
             "lgf_check_conversions": ([P, P, P, P, I], I),
             "lgf_step_fwd": ([P, D, P, P], I),
@@ -237,6 +241,11 @@ class Lattice:
         """FP32 phase: update fused with Delta (True) or the two-kernel form (False, the default)."""
         _check(self._lib.lgf_set_fp32_update(self._h, 1 if fused else 0), "lgf_set_fp32_update")
 
+    def set_accel_precision(self, bits: int):
+        """Mixed contexts: the accelerator's transforms of the FP64 iterations in
+        FP64 (64, the default) or FP32 (32; Delta, theta, F, g and the update stay FP64)."""
+        _check(self._lib.lgf_set_accel_precision(self._h, int(bits)), "lgf_set_accel_precision")
+
     def set_links(self, U):
         p, dev, keep = _in_ptr(U, (4, self.V, 3, 3))
         _check(self._lib.lgf_set_links(self._h, p, dev), "lgf_set_links")
@@ -353,6 +362,24 @@ def _autotune(self) -> None:
 Lattice.autotune = _autotune
 
 
+def _set_shape(self, precision: int = 64, nt_xy: int = 128, nt_zt: int = 128, xw: int = 4, zt_form: int = 0) -> None:
+    """Launch shape of one precision's FFT kernels (zt_form 1: the persistent z,t
+    kernel with TMA-staged pencils); raises LgfError (LGF_ERR_ARG) for a shape the
+    kernels cannot run."""
+    _check(self._lib.lgf_set_shape(self._h, int(precision), int(nt_xy), int(nt_zt), int(xw), int(zt_form)),
+           "lgf_set_shape")
+
+
+def _get_shape(self, precision: int = 64) -> dict:
+    out = (ctypes.c_int * 5)()
+    _check(self._lib.lgf_get_shape(self._h, int(precision), out), "lgf_get_shape")
+    return dict(zip(("nt_xy", "nt_zt", "xw", "zt_form", "zt_grid"), list(out)))
+
+
+Lattice.set_shape = _set_shape
+Lattice.get_shape = _get_shape
+
+
 def probe_fma(precision: int = 64, n_iter: int = 100000) -> dict:
     """FMA rate (GFLOP/s, an FMA counted as two flops) of the current GPU in FP64 or FP32."""
     lib = load()
@@ -465,6 +492,9 @@ class Batch:
 
     def set_switch_tol(self, tol: float):
         _check(self._lib.lgf_batch_set_switch_tol(self._h, float(tol)), "lgf_batch_set_switch_tol")
+
+    def set_accel_precision(self, bits: int):
+        _check(self._lib.lgf_batch_set_accel_precision(self._h, int(bits)), "lgf_batch_set_accel_precision")
 
     def set_links(self, i: int, U):
         p, dev, keep = _in_ptr(U, (4, self.V[i], 3, 3))
