@@ -73,6 +73,9 @@ def parse():
                          "kernels: the iteration kernels launched one by one (FP64 and FP32), per-kernel times; "
                          "probe: the FP64 and FP32 FMA rates of the GPU (the FP64 kernels' arithmetic ceiling)")
     ap.add_argument("--no-autotune", action="store_true", help="--workload kernels: default launch shapes")
+    ap.add_argument("--zt-form", type=int, default=-1, choices=[-1, 0, 1],
+                    help="--workload kernels: z,t kernel form of both precisions (0 pencil-tiled, 1 TMA-staged "
+                         "pencils, 4-column pencils; -1 the default or autotuned shape)")
     ap.add_argument("--beta", type=float, default=6.0, help="coupling of --workload wilson")
     ap.add_argument("--switch-tol", type=float, default=1e-6,
                     help="theta that ends the FP32 phase of --workload ensemble (1e-6 as specified; 1e-13 deep)")
@@ -373,6 +376,41 @@ def run_ours(args, dims):
                                        for k in msf}
         mixed["fp32_fused_iteration_ms"] = sum(msf.values())
         latm.set_fp32_update(False)
+        # the accelerator's transforms in FP32 inside the FP64 iterations (Delta, theta,
+        # F, Gram-Schmidt and update in FP64): whole fixes in FP64 iterations (no FP32
+        # phase) and the mixed mode at both switch points, same steps as above
+        latm.set_accel_precision(32)
+        accel = {}
+        for name, sw in (("fp64_iterations", 1e300), ("mixed_switch_1e-06", 1e-6), ("mixed_switch_1e-13", 1e-13)):
+            latm.set_switch_tol(sw)
+            for k in range(max(1, args.warmup)):
+                mstep(k)
+            torch.cuda.synchronize()
+            eva = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            ainfo = []
+            eva[0].record(stream)
+            for k in range(args.steps):
+                ainfo.append(mstep(k))
+                eva[k + 1].record(stream)
+            torch.cuda.synchronize()
+            aper = [eva[k].elapsed_time(eva[k + 1]) / 1000.0 for k in range(args.steps)]
+            Ta, ait = reduce_over_ranks(pg, sum(aper), sum(r["iters"] for r in ainfo))
+            attt = {}
+            for k, r in enumerate(ainfo):
+                e = str(EPS[k % len(EPS)])
+                f64 = ttt.get(e, {}).get("F")
+                attt.setdefault(e, dict(iters_fp32=r["iters_fp32"], iters_fp64=r["iters_fp64"], ms=1000 * aper[k],
+                                        converged=r["converged"], theta=r["theta"],
+                                        F_rel_diff_vs_fp64=(abs(r["F"] / f64 - 1) if f64 else None)))
+            accel[name] = {"value": ait / Ta, "unit": "iters/s", "ms_per_step": 1000 * Ta / args.steps,
+                           "speedup_time_to_theta_vs_fp64": T / Ta, "time_to_theta": attt}
+        latm.set_switch_tol(1e-6)
+        latm.set_links(dev[1])
+        msa = latm.time_kernels(args.alpha, n_iter=8, precision=64)
+        accel["kernels_fp64_iteration"] = {k: {"ms": msa[k]} for k in msa}
+        accel["fp64_iteration_ms"] = sum(msa.values())
+        mixed["accel_fp32"] = accel
+        latm.set_accel_precision(64)
         latm.close()
 
     # link parametrisation: the same FP64 workload with row 2 kept in memory (18 reals)
@@ -774,16 +812,22 @@ def run_48(args, stream, rank):
     with lgf.Lattice(L, mixed=True, stream=stream) as lm:
         lm.set_links(U)
         lm.autotune()
-        for sw in (1e-6, 1e-13):
-            lm.set_switch_tol(sw)
-            rm, msm = timed(lm)
-            Um = lm.get_links(device="cuda")
-            out["mixed_switch_%g" % sw] = {
-                "ms": msm, "iters_fp32": rm["iters_fp32"], "iters_fp64": rm["iters_fp64"], "F": rm["F"],
-                "converged": rm["converged"], "F_rel_diff_vs_fp64": abs(rm["F"] / r64["F"] - 1),
-                "max_link_diff_vs_fp64": float((Um - U64).abs().max().item()),
-                "speedup_vs_fp64": ms64 / msm}
-            del Um
+        # mixed precision as specified, then with the accelerator's transforms in FP32
+        # inside the FP64 iterations (switch 1e300: every iteration FP64)
+        for accel, runs in ((64, ((1e-6, "mixed_switch_1e-06"), (1e-13, "mixed_switch_1e-13"))),
+                            (32, ((1e300, "fp64_accel_fp32"), (1e-6, "mixed_accel_fp32_switch_1e-06"),
+                                  (1e-13, "mixed_accel_fp32_switch_1e-13")))):
+            lm.set_accel_precision(accel)
+            for sw, name in runs:
+                lm.set_switch_tol(sw)
+                rm, msm = timed(lm)
+                Um = lm.get_links(device="cuda")
+                out[name] = {
+                    "ms": msm, "iters_fp32": rm["iters_fp32"], "iters_fp64": rm["iters_fp64"], "F": rm["F"],
+                    "converged": rm["converged"], "F_rel_diff_vs_fp64": abs(rm["F"] / r64["F"] - 1),
+                    "max_link_diff_vs_fp64": float((Um - U64).abs().max().item()),
+                    "speedup_vs_fp64": ms64 / msm}
+                del Um
     del U64, U
     torch.cuda.empty_cache()
     return out
@@ -816,11 +860,16 @@ def ensemble_leg(args, stream, rank):
 
         b.set_switch_tol(1e-6)
         one_pass()  # warm-up
-        for sw in (1e-6, 1e-13):
+        for accel, sw in ((64, 1e-6), (64, 1e-13), (32, 1e-6), (32, 1e-13)):
+            if accel == 32 and sw == 1e-6:
+                # the accelerator's transforms in FP32 inside the FP64 iterations
+                b.set_accel_precision(32)
+                b.set_switch_tol(sw)
+                one_pass()  # warm-up of the new graph
             b.set_switch_tol(sw)
             r, ms = one_pass()
             tt = np.array(r["t_retire_ms"])
-            out["switch_%g" % sw] = {
+            out[("switch_%g" if accel == 64 else "accel_fp32_switch_%g") % sw] = {
                 "ms": ms, "configs_per_hour": len(dims) / ms * 3.6e6,
                 "time_to_theta_ms": {"p50": float(np.percentile(tt, 50)), "p99": float(np.percentile(tt, 99)),
                                      "max": float(tt.max())},
@@ -1019,14 +1068,20 @@ def run_kernels(args, dims):
         lat.set_links(U)
         if not args.no_autotune:
             lat.autotune()
+        if args.zt_form >= 0:
+            lat.set_shape(64, nt_xy=128, nt_zt=128, xw=4, zt_form=args.zt_form)
+            lat.set_shape(32, nt_xy=128, nt_zt=256, xw=4, zt_form=args.zt_form)
+        out["shapes"] = {"fp64": lat.get_shape(64), "fp32": lat.get_shape(32)}
         # FP64, FP32 in the two-kernel form (the default), FP32 with the update
-        # fused with Delta
-        for name, prec, fused in (("fp64", 64, False), ("fp32", 32, False), ("fp32_fused", 32, True)):
+        # fused with Delta, FP64 iterations with the accelerator's transforms in FP32
+        for name, prec, fused in (("fp64", 64, False), ("fp32", 32, False), ("fp32_fused", 32, True),
+                                  ("fp64_accel_fp32", 64, False)):
             lat.set_fp32_update(fused)
+            lat.set_accel_precision(32 if name == "fp64_accel_fp32" else 64)
             if args.warmup:
                 lat.time_kernels(args.alpha, n_iter=args.warmup, precision=prec)
             ms = lat.time_kernels(args.alpha, n_iter=max(1, args.steps), precision=prec)
-            per = roofline.per_site(dims, prec, fused)
+            per = roofline.per_site(dims, prec, fused, accel32=(name == "fp64_accel_fp32"))
             out[name] = {k: {"ms": ms[k], "gbs": per[k]["bytes"] * V / ms[k] / 1e6,
                              "hbm_frac_of_measured": per[k]["bytes"] * V / ms[k] / 1e6 / hbm,
                              "gflops": per[k]["flops"] * V / ms[k] / 1e6} for k in ms}

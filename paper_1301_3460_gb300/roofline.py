@@ -31,6 +31,13 @@ phase's other form fuses Delta into the update (fused32=True):
                 as above, the four entering it recomputed for their anti-Hermitian
                 parts (4 x (42 + 2 x 132 + 42 + 12)), G, Delta (64), theta and F (21).
 
+FP64 iterations with the accelerator's transforms in FP32 (accel32=True): the
+update as in FP64; the other three kernels move FP32 fields:
+  delta_xyfft   reads the FP64 packed parts and Re Tr, writes the four FP32 fields:
+                256 + 8 + 32 B (flops as in FP64).
+  zt_fft_accel  the FP32 phase's kernel: 32 + 32 B.
+  xyifft_g      reads the FP32 fields, writes the FP64 g: 32 + 144 B.
+
 Wilson-action generation (k_wilson, one launch per direction and checkerboard
 parity), per link updated, with full 3x3 complex products of 198 flops (27
 complex multiplies, 18 complex adds) and 216 when accumulated into a sum:
@@ -51,7 +58,7 @@ import math
 KERNELS = ("delta_xyfft", "zt_fft_accel", "xyifft_g", "update")
 
 
-def per_site(dims, precision: int = 64, fused32: bool = False) -> dict:
+def per_site(dims, precision: int = 64, fused32: bool = False, accel32: bool = False) -> dict:
     Lx, Ly, Lz, Lt = (int(v) for v in dims)
     w = 1.0 if precision == 64 else 0.5
     lxy = math.log2(Lx * Ly)
@@ -64,6 +71,14 @@ def per_site(dims, precision: int = 64, fused32: bool = False) -> dict:
             "update": dict(bytes=(384 + 144 + 96 + 384 + 96 + 64) * w,
                            flops=4 * (42 + 2 * 132 + 42 + 12 + 2) + 4 * (42 + 2 * 132 + 42 + 12) + 42 + 132
                            + 64 + 21),
+        }
+    if precision == 64 and accel32:
+        return {
+            "delta_xyfft": dict(bytes=256 + 8 + 32, flops=64 + 21 + 4 * 5 * lxy),
+            "zt_fft_accel": dict(bytes=32 + 32, flops=2 * 4 * 5 * lzt + 8),
+            "xyifft_g": dict(bytes=32 + 144, flops=4 * 5 * lxy + 134),
+            "update": dict(bytes=384 + 144 + 96 + 384 + 96 + 256 + 8,
+                           flops=4 * (42 + 2 * 132 + 42 + 12 + 2) + 42 + 132),
         }
     return {
         "delta_xyfft": dict(bytes=(256 + 8 + 64) * w, flops=64 + 21 + 4 * 5 * lxy),
