@@ -437,6 +437,31 @@ def run_ours(args, dims):
         l18.close()
         links18 = {"value": n18 / T18, "unit": "iters/s", "ms_per_step": 1000 * T18 / args.steps,
                    "update_ms": ms18["update"], "kernels_ms": ms18}
+        # the 18-real form with the accelerator's transforms in FP32 inside the FP64
+        # iterations (a mixed context whose FP32 phase is empty: switch above theta)
+        if not args.no_mixed:
+            la = lgf.Lattice(dims, mixed=True, links18=True, stream=stream)
+            la.set_accel_precision(32)
+            la.set_switch_tol(1e300)
+            la.set_links(dev[1])
+            la.autotune()
+            la.set_links(dev[0])
+            la.fix(args.alpha, args.tol, args.max_iter)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            na = 0
+            e0.record(stream)
+            for k in range(args.steps):
+                la.set_links(dev[k % len(dev)])
+                na += la.fix(args.alpha, args.tol, args.max_iter)["iters"]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            Ta = e0.elapsed_time(e1) / 1000.0
+            la.set_links(dev[1])
+            msa = la.time_kernels(args.alpha, n_iter=8, precision=64)
+            la.close()
+            links18["accel_fp32"] = {"value": na / Ta, "unit": "iters/s", "ms_per_step": 1000 * Ta / args.steps,
+                                     "iteration_ms": sum(msa.values()), "kernels_ms": msa}
 
     # the 8-real form: a third of the 12-real link bytes, more FP64 work per load and store
     links8 = None
