@@ -363,6 +363,15 @@ def run_ours(args, dims):
         mixed["time_to_theta_switch_1e-13"] = deep
         latm.set_switch_tol(1e-6)
         latm.set_links(dev[1])
+        # per-kernel times of the two-kernel FP32 form; the default (persistent) form runs
+        # its g builder and update as one launch, timed beside them
+        latm.set_fp32_update(2)
+        msp = latm.time_kernels(args.alpha, n_iter=8, precision=32)
+        mixed["kernels_fp32_persistent"] = {"delta_xyfft": msp["delta_xyfft"], "zt_fft_accel": msp["zt_fft_accel"],
+                                            "g_and_update": msp["xyifft_g"] + msp["update"]}
+        mixed["fp32_persistent_iteration_ms"] = sum(msp.values())
+        latm.set_fp32_update(0)
+        latm.set_links(dev[1])
         msm = latm.time_kernels(args.alpha, n_iter=8, precision=32)
         per32 = roofline.per_site(dims, 32, fused32=False)
         mixed["kernels_fp32"] = {k: {"ms": msm[k], "gbs": per32[k]["bytes"] * V / msm[k] / 1e6,
@@ -375,7 +384,7 @@ def run_ours(args, dims):
         mixed["kernels_fp32_fused"] = {k: {"ms": msf[k], "gbs": perf[k]["bytes"] * V / msf[k] / 1e6}
                                        for k in msf}
         mixed["fp32_fused_iteration_ms"] = sum(msf.values())
-        latm.set_fp32_update(False)
+        latm.set_fp32_update(2)
         # the accelerator's transforms in FP32 inside the FP64 iterations (Delta, theta,
         # F, Gram-Schmidt and update in FP64): whole fixes in FP64 iterations (no FP32
         # phase) and the mixed mode at both switch points, same steps as above
@@ -1097,21 +1106,27 @@ def run_kernels(args, dims):
             lat.set_shape(64, nt_xy=128, nt_zt=128, xw=4, zt_form=args.zt_form)
             lat.set_shape(32, nt_xy=128, nt_zt=256, xw=4, zt_form=args.zt_form)
         out["shapes"] = {"fp64": lat.get_shape(64), "fp32": lat.get_shape(32)}
-        # FP64, FP32 in the two-kernel form (the default), FP32 with the update
-        # fused with Delta, FP64 iterations with the accelerator's transforms in FP32
-        for name, prec, fused in (("fp64", 64, False), ("fp32", 32, False), ("fp32_fused", 32, True),
-                                  ("fp64_accel_fp32", 64, False)):
-            lat.set_fp32_update(fused)
+        # FP64, FP32 in the two-kernel form, FP32 with the update fused with Delta,
+        # FP64 iterations with the accelerator's transforms in FP32, and the FP32 phase's
+        # default form (g builder and update in one persistent launch: both in the
+        # g builder's slot)
+        for name, prec, form in (("fp64", 64, 0), ("fp32", 32, 0), ("fp32_fused", 32, 1),
+                                 ("fp64_accel_fp32", 64, 0), ("fp32_persistent", 32, 2)):
+            lat.set_fp32_update(form)
             lat.set_accel_precision(32 if name == "fp64_accel_fp32" else 64)
             if args.warmup:
                 lat.time_kernels(args.alpha, n_iter=args.warmup, precision=prec)
             ms = lat.time_kernels(args.alpha, n_iter=max(1, args.steps), precision=prec)
-            per = roofline.per_site(dims, prec, fused, accel32=(name == "fp64_accel_fp32"))
+            out[name + "_iteration_ms"] = sum(ms.values())
+            if form == 2:
+                out[name] = {"delta_xyfft": {"ms": ms["delta_xyfft"]}, "zt_fft_accel": {"ms": ms["zt_fft_accel"]},
+                             "g_and_update": {"ms": ms["xyifft_g"] + ms["update"]}}
+                continue
+            per = roofline.per_site(dims, prec, form == 1, accel32=(name == "fp64_accel_fp32"))
             out[name] = {k: {"ms": ms[k], "gbs": per[k]["bytes"] * V / ms[k] / 1e6,
                              "hbm_frac_of_measured": per[k]["bytes"] * V / ms[k] / 1e6 / hbm,
                              "gflops": per[k]["flops"] * V / ms[k] / 1e6} for k in ms}
-            out[name + "_iteration_ms"] = sum(ms.values())
-        lat.set_fp32_update(False)
+        lat.set_fp32_update(2)
     print(json.dumps(out), flush=True)
     return 0
 

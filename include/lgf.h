@@ -179,16 +179,21 @@ int lgf_set_switch_tol(lgf_ctx* ctx, double switch_tol);
 int lgf_set_fp32_refresh(lgf_ctx* ctx, int every);
 
 /*
- * LGF_MIXED: the form of the FP32 phase's update.  fused = 1: one kernel
+ * LGF_MIXED: the form of the FP32 phase's update.  form = 0: the update writes
+ * each new link's packed anti-Hermitian part and Re Tr, and a separate kernel
+ * forms Delta from them (the FP64 phase's form).  form = 2 (default): as 0, with
+ * the g builder (inverse x,y transform and FP64 Gram-Schmidt) and the update in
+ * one persistent launch whose blocks take xy-planes from a queue, each update
+ * waiting (bounded, on per-plane flags) for the g of the planes it reads, so
+ * that building g (FP64 pipe) and updating links (HBM) run side by side on the
+ * device; its results are bit-identical to form 0.  form = 1: one kernel
  * updates the links and forms Delta, theta and F of the new links, recomputing
  * the anti-Hermitian part of each link that enters a site from its neighbour's
- * old link (the links alternate between two FP32 buffers).  fused = 0 (default):
- * the update writes each new link's packed anti-Hermitian part and Re Tr, and a
- * separate kernel forms Delta from them (the FP64 phase's form; the faster of
- * the two on GB300).  Results agree to FP32 rounding; the setting only changes
- * the kernels' work.  Other values: LGF_ERR_ARG.
+ * old link (the links alternate between two FP32 buffers); it agrees with forms
+ * 0 and 2 to FP32 rounding.  The setting only changes the kernels' work.  Other
+ * values: LGF_ERR_ARG; form 2 outside a mixed context: LGF_ERR_STATE.
  */
-int lgf_set_fp32_update(lgf_ctx* ctx, int fused);
+int lgf_set_fp32_update(lgf_ctx* ctx, int form);
 
 /*
  * LGF_MIXED: precision of the accelerator (forward 4D FFT of Delta, the
@@ -331,6 +336,7 @@ int lgf_batch_create(int n, const int* dims, int flags, lgf_batch** out);
 int lgf_batch_set_stream(lgf_batch* b, void* cuda_stream);
 int lgf_batch_set_switch_tol(lgf_batch* b, double switch_tol);  /* every lattice, as lgf_set_switch_tol */
 int lgf_batch_set_accel_precision(lgf_batch* b, int precision);  /* every lattice, as lgf_set_accel_precision */
+int lgf_batch_set_fp32_update(lgf_batch* b, int form);  /* every lattice, as lgf_set_fp32_update */
 int lgf_batch_set_links(lgf_batch* b, int i, const double* U, int on_device);
 int lgf_batch_fix(lgf_batch* b, double alpha, double theta_tol, int max_iter, int* iters, double* F, double* theta,
                   int* status, double* t_retire_ms);

@@ -95,6 +95,8 @@ struct lgf_ctx {
     float* Fs32 = nullptr;    // parts and Re Tr handed from the update to the Delta kernel
     bool fused32 = false;     // FP32 phase: update fused with Delta (links recomputed) or not
     bool accel32 = false;     // FP64 iterations take the accelerator's transforms in FP32
+    bool gu32 = false;        // FP32 phase: g builder and update in one persistent launch
+    unsigned* gu_sync = nullptr;  // its queue, epoch and per-plane flags
     void* Fd = nullptr;       // [4][V] double2 (the FP32 phase uses the front half as float2)
     double2* AH64 = nullptr;  // [4][4][V] packed anti-Hermitian parts of the links
     double* Fs64 = nullptr;   // [V] Re Tr of the four links of a site
@@ -228,7 +230,7 @@ void launch_body32(lgf_ctx* c, cudaStream_t s, const float2* src, float2* dst)
         launch_build_g<float>(d, s, Fd, c->g32, c->ctl);
     } else {
         launch_zt<float>(d, c->sh32, c->tb, s, Fd, c->ctl);
-        launch_xyinv_g<float>(d, c->sh32, c->tb, s, Fd, c->g32, c->ctl);
+        if (!c->gu32 || c->fused32) launch_xyinv_g<float>(d, c->sh32, c->tb, s, Fd, c->g32, c->ctl);
     }
     if (c->fused32) {
         launch_update_delta32(d, s, src, dst, c->G32, c->g32, c->ctl, Fd, c->partials, c->hist);
@@ -238,7 +240,10 @@ void launch_body32(lgf_ctx* c, cudaStream_t s, const float2* src, float2* dst)
         }
         if (!c->plain) launch_xy_fft<float>(d, c->sh32, c->tb, s, Fd, false);
     } else {
-        launch_update<float>(d, s, c->U32, c->G32, c->g32, c->ctl, c->AH32, c->Fs32);
+        if (c->gu32 && !c->plain)
+            launch_gu32(d, c->sh32, s, Fd, c->g32, c->U32, c->G32, c->AH32, c->Fs32, c->ctl, c->gu_sync);
+        else
+            launch_update<float>(d, s, c->U32, c->G32, c->g32, c->ctl, c->AH32, c->Fs32);
         if (c->refresh_every > 0)
             launch_refresh32(s, d, c->lat.ne, c->U64, c->G32, c->U32, c->AH32, c->Fs32, c->ctl, c->refresh_every);
         launch_delta<float>(d, c->sh32, c->tb, s, c->AH32, c->Fs32, Fd, c->partials, c->ctl, c->hist, !c->plain);
@@ -507,6 +512,11 @@ int create_impl(const int dims[4], int flags, lgf_ctx* c)
         CKR(alloc((void**)&c->Fs32, Vs * sizeof(float)));
         CKR(alloc((void**)&c->G32, 6 * Vs * sizeof(float2)));
         CKR(alloc((void**)&c->g32, 9 * Vs * sizeof(float2)));
+        // the FP32 phase's default form: g builder and update in one persistent launch
+        CK(gu32_prepare(c->lat32));
+        CKR(alloc((void**)&c->gu_sync, (size_t)(4 + d.nplanes) * sizeof(unsigned)));
+        CK(cudaMemset(c->gu_sync, 0, (size_t)(4 + d.nplanes) * sizeof(unsigned)));
+        c->gu32 = true;
     }
     // block partial sums of theta and F: one pair per plane (Delta kernel) or per
     // block of the site-parallel kernels, whichever grid is larger
@@ -528,7 +538,7 @@ void free_all(lgf_ctx* c)
     if (c->exec) cudaGraphExecDestroy(c->exec);
     void* ptrs[] = {c->U64, c->G64, c->g64, c->U32, c->G32, c->g32, c->Fd, c->partials, c->ctl, c->ctl_stage,
                     c->hist, c->err, c->stage, c->tables, c->mult, c->AH64, c->Fs64, c->U32b, c->AH32, c->Fs32, c->dGp, c->dGud, c->dQ, c->dGgs, c->dFA, c->dFB,
-                    c->gl_part, c->gl_At, c->gl_D, c->wil_part, c->gen32};
+                    c->gl_part, c->gl_At, c->gl_D, c->wil_part, c->gen32, c->gu_sync};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_ctl) cudaFreeHost(c->host_ctl);
@@ -949,11 +959,21 @@ int lgf_set_accel_precision(lgf_ctx* c, int precision)
     return LGF_OK;
 }
 
-int lgf_set_fp32_update(lgf_ctx* c, int fused)
+int lgf_set_fp32_update(lgf_ctx* c, int form)
 {
-    if (!c || (fused != 0 && fused != 1)) return LGF_ERR_ARG;
-    if (c->fused32 != (fused == 1)) {
-        c->fused32 = fused == 1;
+    if (!c || form < 0 || form > 2) return LGF_ERR_ARG;
+    if (form == 2) {
+        if (!c->mixed) return LGF_ERR_STATE;
+        if (!c->gu_sync) {
+            CK(gu32_prepare(c->lat32));
+            CKR(alloc((void**)&c->gu_sync, (size_t)(4 + c->lat32.nplanes) * sizeof(unsigned)));
+            CK(cudaMemsetAsync(c->gu_sync, 0, (size_t)(4 + c->lat32.nplanes) * sizeof(unsigned), c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+    }
+    if (c->fused32 != (form == 1) || c->gu32 != (form == 2)) {
+        c->fused32 = form == 1;
+        c->gu32 = form == 2;
         drop_graph(c);
     }
     return LGF_OK;
@@ -1294,12 +1314,17 @@ int lgf_time_kernels(lgf_ctx* c, double alpha, int n_iter, int precision, double
             cudaEventRecord(ev[1], s);
             launch_zt<float>(c->lat32, c->sh32, c->tb, s, Fd, c->ctl_stage);
             cudaEventRecord(ev[2], s);
-            launch_xyinv_g<float>(c->lat32, c->sh32, c->tb, s, Fd, c->g32, c->ctl_stage);
+            // the persistent g-and-update form: both in the g builder's slot, none in the update's
+            if (c->gu32 && !c->fused32)
+                launch_gu32(c->lat32, c->sh32, s, Fd, c->g32, c->U32, c->G32, c->AH32, c->Fs32, c->ctl_stage,
+                            c->gu_sync);
+            else
+                launch_xyinv_g<float>(c->lat32, c->sh32, c->tb, s, Fd, c->g32, c->ctl_stage);
             cudaEventRecord(ev[3], s);
             if (c->fused32)
                 launch_update_delta32(c->lat32, s, (it & 1) ? c->U32b : c->U32, (it & 1) ? c->U32 : c->U32b,
                                       c->G32, c->g32, c->ctl_stage, Fd, c->partials, nullptr);
-            else
+            else if (!c->gu32)
                 launch_update<float>(c->lat32, s, c->U32, c->G32, c->g32, c->ctl_stage, c->AH32, c->Fs32);
         }
         cudaEventRecord(ev[4], s);
@@ -1418,6 +1443,16 @@ int lgf_batch_set_switch_tol(lgf_batch* b, double tol)
 {
     if (!b || !(tol >= 0)) return LGF_ERR_ARG;
     for (lgf_ctx* c : b->ctx) c->switch_tol = tol;
+    return LGF_OK;
+}
+
+int lgf_batch_set_fp32_update(lgf_batch* b, int form)
+{
+    if (!b) return LGF_ERR_ARG;
+    CK(cudaStreamSynchronize(b->stream));
+    for (lgf_ctx* c : b->ctx) CKR(lgf_set_fp32_update(c, form));
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
     return LGF_OK;
 }
 

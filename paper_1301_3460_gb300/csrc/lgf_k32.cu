@@ -13,6 +13,42 @@ void launch_update_delta32(const Lat& d, cudaStream_t s, const float2* Uin, floa
     k_update_delta<float><<<update_grid(d.V), 256, 0, s>>>(d, Uin, Uout, G, g, ctl, Fd, partials, hist);
 }
 
+cudaError_t gu32_prepare(const Lat& d)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    if ((e = allow_max_smem(k_gu<float, 32>, optin))) return e;
+    return allow_max_smem(k_gu<float, 128>, optin);
+}
+
+// Grid: the blocks the device holds at once (a persistent launch); lag of the
+// queue: about that many items ahead, in t-steps of 2 Lz items.
+void launch_gu32(const Lat& d, const Shape& sh, cudaStream_t s, const float2* Fd, float2* g, float2* U, float2* G,
+                 float2* AH, float* Fs, Ctl* ctl, unsigned* sync)
+{
+    const size_t sm = xy_smem<float>(d);
+    const bool small = small_plane<float>(d);
+    int dev = 0, nsm = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (small)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gu<float, 32>, sh.nt_xy, sm);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gu<float, 128>, sh.nt_xy, sm);
+    if (per_sm < 1) per_sm = 1;
+    int grid = per_sm * nsm;
+    if (grid > 2 * d.nplanes) grid = 2 * d.nplanes;
+    const int Lz = d.L[2], Lt = d.L[3];
+    int lag = (grid + 2 * Lz - 1) / (2 * Lz);
+    lag = lag < 1 ? 1 : (lag > Lt ? Lt : lag);
+    if (small)
+        k_gu<float, 32><<<grid, sh.nt_xy, sm, s>>>(d, Fd, g, U, G, AH, Fs, ctl, sync, lag);
+    else
+        k_gu<float, 128><<<grid, sh.nt_xy, sm, s>>>(d, Fd, g, U, G, AH, Fs, ctl, sync, lag);
+}
+
 void launch_delta_links32(const Lat& d, cudaStream_t s, const float2* U, float2* Fd, double* partials, Ctl* ctl,
                           double2* hist, int every)
 {

@@ -648,18 +648,15 @@ __device__ __forceinline__ void reunit_rows(cx<double>* X /* 6 in */, cx<double>
     complete_row2(g, g + 6);
 }
 
-// One block per xy-plane: inverse transform along y (columns read from Fd) and x
-// (rows of the plane tile), then g = reunit(1 + alpha/2 Delta~) by row
+// One xy-plane by one block: inverse transform along y (columns read from Fd)
+// and x (rows of the plane tile sm), then g = reunit(1 + alpha/2 Delta~) by row
 // Gram-Schmidt in FP64 whatever T is; g stored as TG.
 template <typename T, typename TG, int LMAX>
-__global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
-                                                 vec2_t<TG>* __restrict__ g, const Ctl* ctl)
+__device__ __forceinline__ void xyinv_g_plane(const Lat& d, const vec2_t<T>* __restrict__ Fd,
+                                              vec2_t<TG>* __restrict__ g, const Ctl* ctl, int plane, vec2_t<T>* sm)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
-    if (ld_flag(&ctl->phase_done)) return;
     const int P = d.P, V = d.V, Lx = d.L[0];
-    const int s0 = blockIdx.x * P;
+    const int s0 = plane * P;
     const int rsx = plane_rsx(d), fs = plane_fs(d);
     plane_y_lines<T, true, LMAX>(d, Fd + s0, V, Lx, sm, fs, rsx);
     __syncthreads();
@@ -708,6 +705,17 @@ __global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k
 #pragma unroll
         for (int e = 0; e < 9; e++) st<TG>(g + (size_t)e * V + s0 + xy, gs[e]);
     }
+}
+
+// One block per xy-plane (xyinv_g_plane).
+template <typename T, typename TG, int LMAX>
+__global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_xyinv_g(Lat d, const vec2_t<T>* __restrict__ Fd,
+                                                 vec2_t<TG>* __restrict__ g, const Ctl* ctl)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    if (ld_flag(&ctl->phase_done)) return;
+    xyinv_g_plane<T, TG, LMAX>(d, Fd, g, ctl, blockIdx.x, sm);
 }
 
 // g(x) = reunit(1 + alpha/2 D(x)) from the four packed spatial fields D (plain
@@ -791,6 +799,37 @@ __device__ __forceinline__ void gauge_accumulate(vec2_t<T>* __restrict__ G, int 
 // One thread per site.  G may be null (gauge not tracked).  Also writes the
 // packed anti-Hermitian parts of the new links (AH) and their Re Tr per site
 // (Fs) for the next Delta.
+// The update of site s (see k_update); ldg(e, site) loads entry e of g at site.
+template <typename T, typename LDG>
+__device__ __forceinline__ void update_site(const Lat& d, vec2_t<T>* __restrict__ U, vec2_t<T>* __restrict__ G,
+                                            LDG ldg, vec2_t<T>* __restrict__ AH, T* __restrict__ Fs, int s)
+{
+    const int V = d.V;
+    int c[4];
+    site_coords(d, s, c);
+    cx<T> gx[9];
+#pragma unroll
+    for (int e = 0; e < 9; e++) gx[e] = ldg(e, s);
+    T f = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        cx<T> u[9], gn[9], w[9];
+        load_link<T>(U, V, d.ne, mu, s, u);
+        const int sn = site_shift(d, s, c[mu], mu, +1);
+#pragma unroll
+        for (int e = 0; e < 9; e++) gn[e] = ldg(e, sn);
+        link_gug(gx, u, gn, w);
+        store_link<T>(U, V, d.ne, mu, s, w);
+        cx<T> a[4];
+        ah_pack(w, a);
+#pragma unroll
+        for (int k = 0; k < 4; k++) st<T>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
+        f += w[0].re + w[4].re + w[8].re;
+    }
+    Fs[s] = f;
+    if (G != nullptr) gauge_accumulate<T>(G, V, s, gx);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, vec2_t<T>* __restrict__ U,
                                                                         vec2_t<T>* __restrict__ G,
@@ -806,26 +845,127 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
     const int V = d.V;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
-    int c[4];
-    site_coords(d, s, c);
-    cx<T> gx[9];
-    load_g<T>(g, V, s, gx);
-    T f = 0;
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        cx<T> u[9], gn[9], w[9];
-        load_link<T>(U, V, d.ne, mu, s, u);
-        load_g<T>(g, V, site_shift(d, s, c[mu], mu, +1), gn);
-        link_gug(gx, u, gn, w);
-        store_link<T>(U, V, d.ne, mu, s, w);
-        cx<T> a[4];
-        ah_pack(w, a);
-#pragma unroll
-        for (int k = 0; k < 4; k++) st<T>(AH + (size_t)(mu * 4 + k) * V + s, a[k]);
-        f += w[0].re + w[4].re + w[8].re;
+    update_site<T>(d, U, G, [&](int e, int site) { return ld<T>(g + (size_t)e * V + site); }, AH, Fs, s);
+}
+
+// ---------------------------------------------------------------- g builder and update in one launch
+
+// Work queue of the persistent g-and-update kernel over the xy-planes
+// p = z + Lz t: items "build g of plane p" (inverse x,y transform and FP64
+// Gram-Schmidt: the FP64 pipe) and "update the sites of plane p" (HBM).  The
+// update of plane (z, t) reads g at (z, t), (z+1, t) and (z, t+1), so the queue
+// holds the builds of t in [0, lag), then for each t < Lt - lag the builds of
+// t + lag followed by the updates of t, then the updates of the last lag values
+// of t: every update comes after the builds it reads, which blocks that were
+// running took earlier, so waiting for them cannot deadlock; a lag of about the
+// resident blocks over 2 Lz keeps most builds finished before their updates are
+// taken.
+struct GuItem {
+    int build, plane;
+};
+__device__ __forceinline__ GuItem gu_item(int i, int Lz, int Lt, int lag)
+{
+    const int nA = lag * Lz;
+    if (i < nA) return GuItem{1, i};
+    const int j = i - nA, nB = 2 * (Lt - lag) * Lz;
+    if (j < nB) {
+        const int t = j / (2 * Lz), r = j - t * 2 * Lz;
+        return r < Lz ? GuItem{1, (t + lag) * Lz + r} : GuItem{0, t * Lz + (r - Lz)};
     }
-    Fs[s] = f;
-    if (G != nullptr) gauge_accumulate<T>(G, V, s, gx);
+    return GuItem{0, (Lt - lag) * Lz + (j - nB)};
+}
+
+// wait until *flag >= ep (another block's release); false after ~1 s of the
+// global timer
+__device__ __forceinline__ bool wait_flag_ge(const unsigned* flag, unsigned ep)
+{
+    if (*(const volatile unsigned*)flag >= ep) return true;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        for (int k = 0; k < 32; k++)
+            if (*(const volatile unsigned*)flag >= ep) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull) return false;
+        __nanosleep(64);
+    }
+}
+
+// The FP32 phase's g builder and update in one persistent launch (queue above).
+// Sync words (per context, zeroed once): [0] next item, [1] blocks finished,
+// [2] launches completed (the epoch), [3] unused, then one word per plane: the
+// epoch of the launch that last built the plane's g.  A build item ends with a
+// block barrier and a release of its flag by thread 0; an update item's thread 0
+// waits for the three flags it reads and the block then reads g through L2 (it
+// was written in this launch).  A wait that runs out sets Ctl::fault; the last
+// block to finish then stops the loop.  The last block also counts the
+// iteration, resets the queue and advances the epoch.
+template <typename T, int LMAX>
+__global__ void __launch_bounds__(kTileMaxThreads<T>, kTileMinBlocks<T, LMAX>) k_gu(
+    Lat d, const vec2_t<T>* __restrict__ Fd, vec2_t<T>* __restrict__ g, vec2_t<T>* __restrict__ U,
+    vec2_t<T>* __restrict__ G, vec2_t<T>* __restrict__ AH, T* __restrict__ Fs, Ctl* ctl, unsigned* sync, int lag)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec2_t<T>* sm = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    __shared__ int s_item;
+    if (ld_flag(&ctl->phase_done)) return;
+    const int Lz = d.L[2], Lt = d.L[3], P = d.P, V = d.V;
+    const int nitems = 2 * d.nplanes;
+    unsigned* flags = sync + 4;
+    const unsigned ep = *(const volatile unsigned*)(sync + 2) + 1u;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(sync, 1u);
+        __syncthreads();
+        const int i = s_item;
+        __syncthreads();
+        if (i >= nitems) break;
+        const GuItem it = gu_item(i, Lz, Lt, lag);
+        if (it.build) {
+            xyinv_g_plane<T, T, LMAX>(d, Fd, g, ctl, it.plane, sm);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicExch(flags + it.plane, ep);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                const int z = it.plane % Lz, t = it.plane / Lz;
+                const int dep[3] = {it.plane, (z + 1 == Lz ? 0 : z + 1) + Lz * t, z + Lz * (t + 1 == Lt ? 0 : t + 1)};
+                bool ok = true;
+#pragma unroll
+                for (int k = 0; k < 3; k++) ok = wait_flag_ge(flags + dep[k], ep) && ok;
+                if (!ok) atomicExch(&ctl->fault, 1);
+                __threadfence();
+            }
+            __syncthreads();
+            const int s0 = it.plane * P;
+            for (int xy = threadIdx.x; xy < P; xy += blockDim.x)
+                update_site<T>(
+                    d, U, G,
+                    [&](int e, int site) {
+                        const vec2_t<T> v = __ldcg(g + (size_t)e * V + site);
+                        return mk<T>(v.x, v.y);
+                    },
+                    AH, Fs, s0 + xy);
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned tk = atomicAdd(sync + 1, 1u);
+        if (tk == gridDim.x - 1) {
+            ctl->iter += 1;
+            if (ctl->phase == 0) ctl->iter_phase0 += 1;
+            if (ld_flag(&ctl->fault)) {
+                ctl->phase_done = 1;
+                ctl->done = 1;
+            }
+            sync[0] = 0u;
+            sync[1] = 0u;
+            __threadfence();
+            atomicExch(sync + 2, ep);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- fused update and Delta

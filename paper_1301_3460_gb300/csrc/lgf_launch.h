@@ -63,6 +63,13 @@ void launch_update_delta32(const Lat& d, cudaStream_t s, const float2* Uin, floa
 void launch_delta_links32(const Lat& d, cudaStream_t s, const float2* U, float2* Fd, double* partials, Ctl* ctl,
                           double2* hist, int every);
 
+// FP32 phase: the g builder and the update in one persistent launch (k_gu); sync
+// holds 4 + Lz Lt words, zeroed once before the first launch.  gu32_prepare
+// raises the kernel's shared-memory limit.
+cudaError_t gu32_prepare(const Lat& d);
+void launch_gu32(const Lat& d, const Shape& sh, cudaStream_t s, const float2* Fd, float2* g, float2* U, float2* G,
+                 float2* AH, float* Fs, Ctl* ctl, unsigned* sync);
+
 // FP64 iterations with the accelerator in FP32 (FP64 unit): Delta, theta and F
 // from the FP64 packed parts with the forward x,y transform in FP32 (Fd32), and
 // the FP32 inverse x,y transform with the FP64 Gram-Schmidt writing an FP64 g;

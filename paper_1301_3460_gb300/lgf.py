@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
             "lgf_set_fp32_update": ([P, I], I),
             "lgf_set_accel_precision": ([P, I], I),
             "lgf_batch_set_accel_precision": ([P, I], I),
+            "lgf_batch_set_fp32_update": ([P, I], I),
             "lgf_set_loop_bound": ([P, I], I),
             "lgf_delta": ([P, P, I, DP, DP], I),
             "lgf_accelerate": ([P, P, P, I], I),
@@ -237,9 +238,11 @@ class Lattice:
     def set_fp32_refresh(self, every: int):
         _check(self._lib.lgf_set_fp32_refresh(self._h, int(every)), "lgf_set_fp32_refresh")
 
-    def set_fp32_update(self, fused: bool):
-        """FP32 phase: update fused with Delta (True) or the two-kernel form (False, the default)."""
-        _check(self._lib.lgf_set_fp32_update(self._h, 1 if fused else 0), "lgf_set_fp32_update")
+    def set_fp32_update(self, form):
+        """FP32 phase: the two-kernel update (False or 0), the update fused with
+        Delta (True or 1), or the g builder and update in one persistent launch (2,
+        the default)."""
+        _check(self._lib.lgf_set_fp32_update(self._h, int(form)), "lgf_set_fp32_update")
 
     def set_accel_precision(self, bits: int):
         """Mixed contexts: the accelerator's transforms of the FP64 iterations in
@@ -495,6 +498,9 @@ class Batch:
 
     def set_accel_precision(self, bits: int):
         _check(self._lib.lgf_batch_set_accel_precision(self._h, int(bits)), "lgf_batch_set_accel_precision")
+
+    def set_fp32_update(self, form: int):
+        _check(self._lib.lgf_batch_set_fp32_update(self._h, int(form)), "lgf_batch_set_fp32_update")
 
     def set_links(self, i: int, U):
         p, dev, keep = _in_ptr(U, (4, self.V[i], 3, 3))

@@ -129,7 +129,7 @@ def test_fp32_update_forms_reach_the_same_maximum(L, seed):
             assert r["converged"] and r["theta"] < 1e-15 and r["iters_fp32"] > 0
             assert r["F"] == pytest.approx(ref["F"], rel=1e-12)
             np.testing.assert_allclose(orc.gauge_transform(L, U, lat.get_gauge()), lat.get_links(), atol=1e-13)
-        assert lat._lib.lgf_set_fp32_update(lat._h, 2) == lgf.LGF_ERR_ARG
+        assert lat._lib.lgf_set_fp32_update(lat._h, 3) == lgf.LGF_ERR_ARG
 
 
 def test_mixed_max_iter_in_fp32_phase_keeps_progress():
