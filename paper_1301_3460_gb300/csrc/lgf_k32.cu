@@ -23,20 +23,24 @@ cudaError_t gu32_prepare(const Lat& d)
     return allow_max_smem(k_gu<float, 128>, optin);
 }
 
-// Grid: the blocks the device holds at once (a persistent launch); lag of the
-// queue: about that many items ahead, in t-steps of 2 Lz items.
-void launch_gu32(const Lat& d, const Shape& sh, cudaStream_t s, const float2* Fd, float2* g, float2* U, float2* G,
+// Blocks of 256 threads whatever the plane kernels' shape (measured on GB300:
+// 242 against 280 us for the 32^4 g builder and update at 128 threads, where the
+// two-kernel form takes 252-254 us at either size); grid: the blocks the device
+// holds at once (a persistent launch); lag of the queue: about that many items
+// ahead, in t-steps of 2 Lz items.
+void launch_gu32(const Lat& d, const Shape&, cudaStream_t s, const float2* Fd, float2* g, float2* U, float2* G,
                  float2* AH, float* Fs, Ctl* ctl, unsigned* sync)
 {
+    constexpr int nt = 256;
     const size_t sm = xy_smem<float>(d);
     const bool small = small_plane<float>(d);
     int dev = 0, nsm = 1, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (small)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gu<float, 32>, sh.nt_xy, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gu<float, 32>, nt, sm);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gu<float, 128>, sh.nt_xy, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gu<float, 128>, nt, sm);
     if (per_sm < 1) per_sm = 1;
     int grid = per_sm * nsm;
     if (grid > 2 * d.nplanes) grid = 2 * d.nplanes;
@@ -44,9 +48,9 @@ void launch_gu32(const Lat& d, const Shape& sh, cudaStream_t s, const float2* Fd
     int lag = (grid + 2 * Lz - 1) / (2 * Lz);
     lag = lag < 1 ? 1 : (lag > Lt ? Lt : lag);
     if (small)
-        k_gu<float, 32><<<grid, sh.nt_xy, sm, s>>>(d, Fd, g, U, G, AH, Fs, ctl, sync, lag);
+        k_gu<float, 32><<<grid, nt, sm, s>>>(d, Fd, g, U, G, AH, Fs, ctl, sync, lag);
     else
-        k_gu<float, 128><<<grid, sh.nt_xy, sm, s>>>(d, Fd, g, U, G, AH, Fs, ctl, sync, lag);
+        k_gu<float, 128><<<grid, nt, sm, s>>>(d, Fd, g, U, G, AH, Fs, ctl, sync, lag);
 }
 
 void launch_delta_links32(const Lat& d, cudaStream_t s, const float2* U, float2* Fd, double* partials, Ctl* ctl,
