@@ -26,8 +26,10 @@ cudaError_t gu32_prepare(const Lat& d)
 // Blocks of 256 threads whatever the plane kernels' shape (measured on GB300:
 // 242 against 280 us for the 32^4 g builder and update at 128 threads, where the
 // two-kernel form takes 252-254 us at either size); grid: the blocks the device
-// holds at once (a persistent launch); lag of the queue: about that many items
-// ahead, in t-steps of 2 Lz items.
+// holds at once (a persistent launch); lag of the queue: the resident blocks
+// over Lz t-steps (twice as many items as blocks; measured on GB300 against
+// fixed lags 1-48: within 1% of the best at 32^4, 48^4 and 32^3x64, and 3-4%
+// faster than half of it).
 void launch_gu32(const Lat& d, const Shape&, cudaStream_t s, const float2* Fd, float2* g, float2* U, float2* G,
                  float2* AH, float* Fs, Ctl* ctl, unsigned* sync)
 {
@@ -45,7 +47,7 @@ void launch_gu32(const Lat& d, const Shape&, cudaStream_t s, const float2* Fd, f
     int grid = per_sm * nsm;
     if (grid > 2 * d.nplanes) grid = 2 * d.nplanes;
     const int Lz = d.L[2], Lt = d.L[3];
-    int lag = (grid + 2 * Lz - 1) / (2 * Lz);
+    int lag = (grid + Lz - 1) / Lz;
     lag = lag < 1 ? 1 : (lag > Lt ? Lt : lag);
     if (small)
         k_gu<float, 32><<<grid, nt, sm, s>>>(d, Fd, g, U, G, AH, Fs, ctl, sync, lag);

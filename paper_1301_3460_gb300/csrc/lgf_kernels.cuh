@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
 // t + lag followed by the updates of t, then the updates of the last lag values
 // of t: every update comes after the builds it reads, which blocks that were
 // running took earlier, so waiting for them cannot deadlock; a lag of about the
-// resident blocks over 2 Lz keeps most builds finished before their updates are
+// resident blocks over Lz keeps most builds finished before their updates are
 // taken.
 struct GuItem {
     int build, plane;
