@@ -30,10 +30,12 @@ static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in
                              unsigned long long* err, int validate)
 {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;  // link index mu*V + s
+    // squared errors, their square root taken once after the maximum (the square
+    // root is monotone and correctly rounded, so this is the maximum of the errors)
     double e_unit = 0.0, e_det = 0.0, e_form = 0.0;
     if (idx < 4L * V) {
         const int mu = (int)(idx / V), s = (int)(idx - (long)mu * V);
-        const double* p = in + idx * 18;
+        const double* p = in + idx * 18;  // 8-byte loads: the caller's array need not be 16-byte aligned
         cx<double> m[9];
 #pragma unroll
         for (int e = 0; e < 9; e++) m[e] = mk<double>(p[2 * e], p[2 * e + 1]);
@@ -48,7 +50,7 @@ static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in
                 cx<T> r[9];
                 rebuild8<T>(w[1], w[2], w[3], atan2(w[0].im, w[0].re), atan2(w[6].im, w[6].re), r);
 #pragma unroll
-                for (int e = 0; e < 9; e++) e_form = dmax_nan(e_form, (double)sqrt(norm2(r[e] - w[e])));
+                for (int e = 0; e < 9; e++) e_form = dmax_nan(e_form, (double)norm2(r[e] - w[e]));
             }
         } else {
 #pragma unroll
@@ -69,15 +71,17 @@ static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in
             for (int e = 6; e < 9; e++) st<T>(U + (size_t)(mu * 9 + e) * V + s, r[e]);
         }
         if (validate) {
+            // U U^dag is Hermitian: its entries (i, j) with i <= j (the entry (j, i)
+            // is their conjugate up to the last rounding of one product)
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
-                for (int j = 0; j < 3; j++) {
+                for (int j = i; j < 3; j++) {
                     cx<double> acc = cmulc(m[3 * i], m[3 * j]);
                     acc = cmacc(acc, m[3 * i + 1], m[3 * j + 1]);
                     acc = cmacc(acc, m[3 * i + 2], m[3 * j + 2]);
                     if (i == j) acc.re -= 1.0;
-                    e_unit = dmax_nan(e_unit, sqrt(norm2(acc)));
+                    e_unit = dmax_nan(e_unit, norm2(acc));
                 }
             cx<double> r2[3];
             complete_row2(m, r2);  // conj of the cofactor row: det = sum_j m2j conj(r2_j)
@@ -85,7 +89,7 @@ static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in
             det = cmacc(det, m[7], r2[1]);
             det = cmacc(det, m[8], r2[2]);
             det.re -= 1.0;
-            e_det = sqrt(norm2(det));
+            e_det = norm2(det);
             if (!(e_det == e_det)) e_det = 1e300;
         }
     }
@@ -97,9 +101,9 @@ static __global__ void k_pack_links(int V, int ne, const double* __restrict__ in
             e_form = dmax_nan(e_form, __shfl_down_sync(0xffffffffu, e_form, o));
         }
         if ((threadIdx.x & 31) == 0) {
-            atomic_max_nonneg(err, e_unit);
-            atomic_max_nonneg(err + 1, e_det);
-            atomic_max_nonneg(err + 2, e_form);
+            atomic_max_nonneg(err, sqrt(e_unit));
+            atomic_max_nonneg(err + 1, sqrt(e_det));
+            atomic_max_nonneg(err + 2, sqrt(e_form));
         }
     }
 }
