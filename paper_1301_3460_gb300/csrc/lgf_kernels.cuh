@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_update(Lat d, v
 struct GuItem {
     int build, plane;
 };
-__device__ __forceinline__ GuItem gu_item(int i, int Lz, int Lt, int lag)
+__host__ __device__ __forceinline__ GuItem gu_item(int i, int Lz, int Lt, int lag)
 {
     const int nA = lag * Lz;
     if (i < nA) return GuItem{1, i};
